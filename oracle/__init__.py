@@ -1,0 +1,167 @@
+"""ORACLE -- test infrastructure, not the product.
+
+Python access to the plain single-threaded CPU definitions in ``oracle.cpp``
+(filtered group-by with exact int64 aggregates; inner equi-join with payload
+gather).  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  It imports nothing from the
+GPU library and the GPU library imports nothing from it.
+
+Query descriptions are plain dicts:
+    cols  : list of numpy arrays (uint8, int32 or int64)
+    keys  : list of column indices (one column, or several packed, see oracle.cpp)
+    preds : list of (col, lo, hi), inclusive range filters
+    aggs  : list of (op, base_col, [(fcol, c, s), ...]) with op in
+            {"sum", "count", "min", "max"}; the aggregate input of row i is
+            base[i] * prod (c + s * fcol[i]) mod 2^64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
+_TYPES = {np.dtype(np.uint8): 0, np.dtype(np.int32): 1, np.dtype(np.int64): 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            lib.orc_free.argtypes = [vp]
+            lib.orc_groupby.restype = i64
+            lib.orc_groupby.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, i32, vp, vp, vp,
+                                        vp, vp, vp, vp, vp]
+            lib.orc_join.restype = i64
+            lib.orc_join.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp]
+            lib.orc_join_count.restype = i64
+            lib.orc_join_count.argtypes = [vp, i64, vp, i64]
+            _lib = lib
+    return _lib
+
+
+def _arr(values, dtype):
+    a = np.ascontiguousarray(np.asarray(values, dtype=dtype))
+    return a if a.size else np.zeros(1, dtype=dtype)
+
+
+def _take(ptr, n, dtype):
+    """Copy n elements from a malloc'ed oracle buffer and release it."""
+    lib = _L()
+    try:
+        if n == 0:
+            return np.empty(0, dtype=dtype)
+        ct = np.ctypeslib.as_ctypes_type(np.dtype(dtype))
+        buf = ctypes.cast(ptr, ctypes.POINTER(ct * n)).contents
+        return np.frombuffer(buf, dtype=dtype).copy()
+    finally:
+        lib.orc_free(ptr)
+
+
+def groupby(q: dict):
+    """Filtered group-by.  Returns (keys int64[G], aggs int64[A, G]) with groups
+    in ascending signed key order."""
+    cols = [np.ascontiguousarray(c) for c in q["cols"]]
+    n = len(cols[0]) if cols else 0
+    for c in cols:
+        if c.dtype not in _TYPES or len(c) != n:
+            raise ValueError("columns must be uint8/int32/int64 of equal length")
+    ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+    types = _arr([_TYPES[c.dtype] for c in cols], np.int32)
+    keys = _arr(q["keys"], np.int32)
+    preds = q.get("preds", [])
+    pc = _arr([p[0] for p in preds], np.int32)
+    plo = _arr([p[1] for p in preds], np.int64)
+    phi = _arr([p[2] for p in preds], np.int64)
+    aggs = q["aggs"]
+    A = len(aggs)
+    op = _arr([OPS[a[0]] for a in aggs], np.int32)
+    base = _arr([a[1] for a in aggs], np.int32)
+    nf = _arr([len(a[2]) for a in aggs], np.int32)
+    fcol = np.zeros(2 * max(A, 1), np.int32)
+    cc = np.zeros(2 * max(A, 1), np.int64)
+    ss = np.zeros(2 * max(A, 1), np.int64)
+    for a, (_, _, fs) in enumerate(aggs):
+        if len(fs) > 2:
+            raise ValueError("at most two factors per aggregate")
+        for f, (fc, c, s) in enumerate(fs):
+            fcol[2 * a + f], cc[2 * a + f], ss[2 * a + f] = fc, c, s
+    ok_p, oa_p = ctypes.c_void_p(), ctypes.c_void_p()
+    ng = _L().orc_groupby(n, ptrs, types.ctypes.data, len(q["keys"]), keys.ctypes.data,
+                          len(preds), pc.ctypes.data, plo.ctypes.data, phi.ctypes.data, A,
+                          op.ctypes.data, base.ctypes.data, nf.ctypes.data, fcol.ctypes.data,
+                          cc.ctypes.data, ss.ctypes.data, ctypes.byref(ok_p),
+                          ctypes.byref(oa_p))
+    if ng < 0:
+        raise MemoryError("oracle group-by")
+    out_keys = _take(ok_p.value, ng, np.int64)
+    out_aggs = _take(oa_p.value, ng * A, np.int64).reshape(A, ng)
+    return out_keys, out_aggs
+
+
+def join(build_keys, payload, probe_keys):
+    """Inner equi-join bag.  Returns (probe_idx int32, build_idx int32,
+    payload int64) sorted by (probe_idx, build_idx)."""
+    bk = np.ascontiguousarray(build_keys, dtype=np.int64)
+    bp = np.ascontiguousarray(payload, dtype=np.int64)
+    pk = np.ascontiguousarray(probe_keys, dtype=np.int64)
+    a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    n = _L().orc_join(bk.ctypes.data, bp.ctypes.data, len(bk), pk.ctypes.data, len(pk),
+                      ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if n < 0:
+        raise MemoryError("oracle join")
+    return _take(a.value, n, np.int32), _take(b.value, n, np.int32), _take(c.value, n, np.int64)
+
+
+def join_count(build_keys, probe_keys) -> int:
+    bk = np.ascontiguousarray(build_keys, dtype=np.int64)
+    pk = np.ascontiguousarray(probe_keys, dtype=np.int64)
+    return int(_L().orc_join_count(bk.ctypes.data, len(bk), pk.ctypes.data, len(pk)))
+
+
+def lineitem_query(li: dict, date_hi: int = 2430) -> dict:
+    """The fused filter + group-by over lineitem-like columns: keep date <= date_hi,
+    group by (flag, status), sum(qty), sum(price), sum(price*(100-disc)),
+    sum(price*(100-disc)*(100+tax)), count."""
+    cols = [li["flag"], li["status"], li["qty"], li["price"], li["disc"], li["tax"], li["date"]]
+    return {
+        "cols": cols,
+        "keys": [0, 1],
+        "preds": [(6, -(2**31), date_hi)],
+        "aggs": [
+            ("sum", 2, []),
+            ("sum", 3, []),
+            ("sum", 3, [(4, 100, -1)]),
+            ("sum", 3, [(4, 100, -1), (5, 100, 1)]),
+            ("count", 2, []),
+        ],
+    }
+
+
+def kv_query(keys, vals, ops=("sum", "count", "min", "max")) -> dict:
+    """Group-by of one int64 value column by one key column, no filter."""
+    return {"cols": [keys, vals], "keys": [0], "preds": [],
+            "aggs": [(o, 1, []) for o in ops]}
