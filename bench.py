@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Throughput of the relational hot path on one GB300 (or N replicas).
+
+One step = one pass over every built operator on seeded synthetic columns
+(they stand in for the TPC-H data the paper profiles, Sec. 3.2):
+  lineitem  fused filter (date <= 2430) + group-by (flag, status), 5 exact
+            int64 aggregates, 10^6 rows (plan: exact distinct count)
+  join      hash build of 10^6 unique int64 keys + probe of 1.6*10^7 keys
+            (90 % present) emitting (probe_idx, build_idx, payload)
+  zipf      group-by of 2*10^8 (int64 key, int64 value) rows, keys
+            Zipf(1.1) over 10^7 ranks, sum/count/min/max (plan: exact count)
+  fourkeys  the same with 4 distinct keys
+Every call goes through the C ABI of librel.so.  value = rows of all parts /
+device time of the step (inputs resident in HBM); e2e = the same through the
+public API with the inputs copied from pinned host memory and the results
+copied back inside the timed region.  The step reads 6.6 GB, far more than
+the 129 MB L2, so consecutive steps do not hit a warm cache.
+
+--impl reference times the CPU oracle (single-threaded C++) on bounded row
+prefixes of the same parts and extrapolates each part's rows/s linearly.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rows/s & %HBM/instr-issue roofline, groupby+join probe; learned/batched vs plain"
+WORKLOAD = ("lineitem filter+group-by 1e6 rows; join build 1e6 x probe 1.6e7; "
+            "group-by 2e8 rows Zipf(1.1) over 1e7 keys; group-by 2e8 rows 4 keys")
+
+
+def full_sizes(small: bool):
+    if small:
+        return dict(li=100_000, nb=100_000, np=1_600_000, big=20_000_000)
+    return dict(li=1_000_000, nb=1_000_000, np=16_000_000, big=200_000_000)
+
+
+# ----------------------------------------------------------------- inputs
+
+def make_inputs(sz, seed):
+    import oracle  # query description helpers only; no oracle computation here
+    import synth
+
+    li = synth.lineitem(sz["li"], seed=seed)
+    bk, bp = synth.join_build(sz["nb"], seed=seed)
+    pk, _ = synth.join_probe(sz["np"], sz["nb"], seed=seed)
+    zk, zv = synth.zipf_kv(sz["big"], seed=seed)
+    fk, fv = synth.few_keys_kv(sz["big"], n_keys=4, seed=seed)
+    return {"li": oracle.lineitem_query(li), "bk": bk, "bp": bp, "pk": pk,
+            "zipf": oracle.kv_query(zk, zv), "four": oracle.kv_query(fk, fv)}
+
+
+def part_rows(sz):
+    return {"lineitem": sz["li"], "join": sz["nb"] + sz["np"], "zipf": sz["big"],
+            "fourkeys": sz["big"]}
+
+
+def part_bytes(inp):
+    b = {"lineitem": sum(c.nbytes for c in inp["li"]["cols"]),
+         "join": inp["bk"].nbytes + inp["bp"].nbytes + inp["pk"].nbytes,
+         "zipf": sum(c.nbytes for c in inp["zipf"]["cols"]),
+         "fourkeys": sum(c.nbytes for c in inp["four"]["cols"])}
+    return b
+
+
+# ------------------------------------------------------------- GPU parts
+
+class GpuStep:
+    """Device-resident inputs and the calls of one step."""
+
+    def __init__(self, inp, dev):
+        import torch
+
+        from paper_2608_13696_gb300 import rel
+
+        self.torch, self.rel, self.dev = torch, rel, dev
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        self.q = {}
+        for name, key in (("lineitem", "li"), ("zipf", "zipf"), ("fourkeys", "four")):
+            q = dict(inp[key])
+            q["cols"] = [t(c) for c in inp[key]["cols"]]
+            self.q[name] = q
+        self.bk, self.bp, self.pk = t(inp["bk"]), t(inp["bp"]), t(inp["pk"])
+        self.host = inp
+        self.results = {}
+
+    def tensors(self):
+        out = [self.bk, self.bp, self.pk]
+        for q in self.q.values():
+            out += q["cols"]
+        return out
+
+    def part(self, name):
+        rel = self.rel
+        if name == "join":
+            tab = rel.JoinTable(self.bk, self.bp)
+            self.results[name] = tab.probe(self.pk, capacity=self.pk.numel())
+            return
+        q = self.q[name]
+        plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT)
+        self.results[name] = rel.groupby(q, plan=plan)
+        self.results[name + ".plan"] = plan
+
+    def result_tensors(self):
+        out = []
+        for name in ("lineitem", "zipf", "fourkeys"):
+            k, aggs = self.results[name]
+            out += [k, *aggs]
+        out += list(self.results["join"])
+        return out
+
+
+PARTS = ("lineitem", "join", "zipf", "fourkeys")
+# bytes the kernel must move per unit, by (part, kernel): inputs read once,
+# outputs written once; hash-table traffic is not algorithmic
+def algo_bytes(kernel, part, inp, res):
+    cols = {"lineitem": inp["li"]["cols"], "zipf": inp["zipf"]["cols"],
+            "fourkeys": inp["four"]["cols"]}
+    if kernel.startswith("gb_main_") and kernel != "gb_main_keyset":
+        return sum(c.nbytes for c in cols[part])
+    if kernel == "gb_main_keyset":
+        q = {"lineitem": inp["li"], "zipf": inp["zipf"], "fourkeys": inp["four"]}[part]
+        used = set(q["keys"]) | {p[0] for p in q.get("preds", [])}
+        return sum(q["cols"][c].nbytes for c in used)
+    if kernel == "gb_compact":
+        k, aggs = res[part]
+        return (k.numel() * 8) * (1 + len(aggs))
+    if kernel == "join_build":
+        return inp["bk"].nbytes + inp["bp"].nbytes
+    if kernel == "join_probe":
+        return inp["pk"].nbytes + res["join"][0].numel() * 16
+    return 0
+
+
+# ----------------------------------------------------------------- clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU (oracle)
+
+def time_oracle_parts(inp, sz, frac_rows):
+    """Time the oracle on row prefixes; returns {part: (rows, seconds)}."""
+    import oracle
+
+    out = {}
+    n = max(1, int(sz["li"] * frac_rows["lineitem"]))
+    q = dict(inp["li"])
+    q["cols"] = [c[:n] for c in q["cols"]]
+    t = time.perf_counter()
+    oracle.groupby(q)
+    out["lineitem"] = (n, time.perf_counter() - t)
+    npr = max(1, int(sz["np"] * frac_rows["join"]))
+    t = time.perf_counter()
+    oracle.join(inp["bk"], inp["bp"], inp["pk"][:npr])
+    out["join"] = (sz["nb"] + npr, time.perf_counter() - t)
+    for name, key in (("zipf", "zipf"), ("fourkeys", "four")):
+        n = max(1, int(sz["big"] * frac_rows[name]))
+        q = dict(inp[key])
+        q["cols"] = [c[:n] for c in q["cols"]]
+        t = time.perf_counter()
+        oracle.groupby(q)
+        out[name] = (n, time.perf_counter() - t)
+    return out
+
+
+def extrapolate(timings, rows_full):
+    """rows/s of a full step from per-part rates."""
+    secs = sum(rows_full[p] / (r / s) for p, (r, s) in timings.items())
+    return sum(rows_full.values()) / secs, secs
+
+
+CPU_FRACS = {"lineitem": 1.0, "join": 0.125, "zipf": 0.05, "fourkeys": 0.05}
+REF_FRACS = {"lineitem": 0.2, "join": 0.0625, "zipf": 0.01, "fourkeys": 0.01}
+
+
+def sample_text(fr, sz):
+    return (f"oracle on row prefixes: lineitem {int(sz['li'] * fr['lineitem'])}, join build "
+            f"{sz['nb']} + probe {int(sz['np'] * fr['join'])}, zipf "
+            f"{int(sz['big'] * fr['zipf'])}, fourkeys {int(sz['big'] * fr['fourkeys'])} rows; "
+            f"each part's rows/s extrapolated linearly to the full step")
+
+
+# ------------------------------------------------------------------- main
+
+def run_reference(args, sz):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    inp = make_inputs(sz, seed=0)
+    rows_full = part_rows(sz)
+    for _ in range(args.warmup):
+        time_oracle_parts(inp, sz, REF_FRACS)
+    t0 = time.perf_counter()
+    tot = {p: [0, 0.0] for p in PARTS}
+    for _ in range(args.steps):
+        for p, (r, s) in time_oracle_parts(inp, sz, REF_FRACS).items():
+            tot[p][0] += r
+            tot[p][1] += s
+    wall = time.perf_counter() - t0
+    value, secs = extrapolate({p: tuple(v) for p, v in tot.items()}, rows_full)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(rows_full.values()) / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded generators standing in for TPC-H)",
+            "config": {"workload": WORKLOAD, "rows_per_step": sum(rows_full.values())},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_text(REF_FRACS, sz)},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--small", action="store_true", help="10x smaller workload (quick checks)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    sz = full_sizes(args.small)
+    if args.impl == "reference":
+        return run_reference(args, sz)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2608_13696_gb300 import rel
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rel.load()
+
+    inp = make_inputs(sz, seed=rank)
+    rows_full = part_rows(sz)
+    rows_step = sum(rows_full.values())
+    g = GpuStep(inp, dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(timing=None):
+        for p in PARTS:
+            c0 = rel.launch_count()
+            if timing is not None:
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+            g.part(p)
+            if timing is not None:
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev1.record(stream)
+                timing.append((p, ev0, ev1, rel.launch_count() - c0))
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    timing = []
+    with Clocks(local) as clk:
+        rel.profile_start()
+        l0 = rel.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(timing)
+        e1.record(stream)
+        barrier()
+        launches = rel.launch_count() - l0
+        recs = rel.profile_stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = rows_step * world / (ms / 1e3) * args.steps
+
+    # per part and per kernel
+    parts, kern = {}, {}
+    i = 0
+    for p, a, b, n in timing:
+        d = parts.setdefault(p, {"ms": 0.0, "launches": 0})
+        d["ms"] += a.elapsed_time(b) / args.steps
+        d["launches"] += n
+        for name, kms in recs[i:i + n]:
+            kk = kern.setdefault((p, name), [0, 0.0])
+            kk[0] += 1
+            kk[1] += kms
+        i += n
+    for p, d in parts.items():
+        d["rows"] = rows_full[p]
+        d["rows_per_s"] = rows_full[p] / (d["ms"] / 1e3)
+        d["launches"] //= args.steps
+    total_kms = sum(v[1] for v in kern.values()) or 1.0
+    (dp, dk), (dn, dms) = max(kern.items(), key=lambda kv: kv[1][1])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    per_launch_ms = dms / dn
+    abytes = algo_bytes(dk, dp, inp, g.results)
+    achieved = abytes / (per_launch_ms / 1e3) / 1e9
+    kernels = {f"{p}/{k}": {"launches": v[0], "total_ms": v[1], "share": v[1] / total_kms}
+               for (p, k), v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    clocks = clk.summary()
+
+    line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded generators standing in for TPC-H)",
+            "config": {"workload": WORKLOAD, "rows_per_step": rows_step,
+                       "l2": "inputs larger than L2 (6.6 GB read per step)",
+                       "plans": "exact distinct-count pre-pass (the plain form)"},
+            "parts": parts,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved / peak_gbs, "traffic": None,
+                         "kernel": f"{dp}/{dk}", "algo_bytes_per_launch": abytes,
+                         "ms_per_launch": per_launch_ms, "peak_source": peak_src},
+            "gpu_launches": launches, "kernels": kernels, "clocks": clocks}
+
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, g, inp, stream, world, barrier, rows_step)
+    if rank == 0 and not args.no_cpu_baseline:
+        t = time_oracle_parts(inp, sz, CPU_FRACS)
+        v, _ = extrapolate(t, rows_full)
+        line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                                "sample": sample_text(CPU_FRACS, sz)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, g, inp, stream, world, barrier, rows_step):
+    """Same step through the public API with inputs from pinned host memory
+    and every result copied back, copies inside the timed region."""
+    import torch
+    import torch.distributed as dist
+
+    dev_in = g.tensors()
+    host_in = [t.cpu().pin_memory() for t in dev_in]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = [0]
+
+    def e2e_step():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        for p in PARTS:
+            g.part(p)
+        outs = g.result_tensors()
+        hs = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        for h, o in zip(hs, outs):
+            h.copy_(o, non_blocking=True)
+        d2h[0] = sum(o.numel() * o.element_size() for o in outs)
+        return hs
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=stream.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"value": rows_step * world * args.steps / (ms / 1e3), "unit": "rows/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h[0],
+            "ms_per_step": ms / args.steps}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

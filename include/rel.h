@@ -1,0 +1,238 @@
+/*
+ * rel.h -- C ABI of the GB300 (sm_103a) relational hot path: a fused
+ * filter + hash group-by with exact int64 aggregates, and a hash equi-join
+ * (build, count, probe with match-pair emission and payload gather).
+ *
+ * What the operators compute follows the paper's statement of the profiled
+ * relational operators (arxiv 2608.13696): columnar, Arrow-like inputs and an
+ * operator API that runs one or more kernels per call (Sec. 2.3); group-by
+ * aggregation in shared memory (Sec. 7, single_pass_shmem_aggs_kernel);
+ * expressions evaluated inside the operator instead of by an interpreter
+ * (Sec. 7, compute_column_kernel); the join's build / count / retrieve steps
+ * over a hash table read randomly (Sec. 7, insert_if_n, count, retrieve) and
+ * the gather out[i] = in[map[i]] (Sec. 7, transform_kernel).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *data, keys, payload, out_* and ws are DEVICE pointers
+ *    owned by the caller; the library never allocates device or pinned
+ *    memory.  Descriptors, plans, rel_join_table and *_host pointers are HOST
+ *    memory owned by the caller.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  A call that writes a *_host count synchronises that stream
+ *    before returning; with a NULL *_host pointer the call does not block.
+ *  - Errors are return codes (rel_status); nothing throws across the ABI.
+ *    rel_last_error() gives a thread-local message for the last failure.
+ *  - Result rows come in an unspecified order.
+ *  - Every device-side wait is bounded; a wait that gives up returns
+ *    REL_E_TIMEOUT instead of hanging.
+ */
+#ifndef REL_H
+#define REL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rel_status;
+#define REL_OK 0
+#define REL_E_INVALID (-1)     /* bad descriptor, size or pointer              */
+#define REL_E_CAPACITY (-2)    /* output or workspace too small; see *_host    */
+#define REL_E_CUDA (-3)        /* a CUDA runtime call failed                   */
+#define REL_E_TIMEOUT (-4)     /* a bounded device-side wait gave up           */
+#define REL_E_UNSUPPORTED (-5) /* valid request outside this build's limits    */
+#define REL_E_OVERFLOW (-6)    /* hash table sized by the plan was too small   */
+
+/* column element types */
+#define REL_U8 0
+#define REL_I32 1
+#define REL_I64 2
+
+/* aggregate operators */
+#define REL_SUM 0
+#define REL_COUNT 1
+#define REL_MIN 2
+#define REL_MAX 3
+
+/* group-by variants (a plan's choice; results never depend on it) */
+#define REL_VAR_AUTO 0        /* let rel_plan_size choose                       */
+#define REL_VAR_SMEM 1        /* per-CTA shared-memory tables, merged at the end */
+#define REL_VAR_GLOBAL 2      /* one global open-addressing table               */
+#define REL_VAR_PARTITIONED 3 /* reserved: radix partition, then per-part agg   */
+
+/* limits of one group-by descriptor */
+#define REL_MAX_COLS 8
+#define REL_MAX_KEYS 4
+#define REL_MAX_PREDS 4
+#define REL_MAX_AGGS 8
+
+typedef struct {
+  const void* data; /* device pointer, n_rows elements of `type`            */
+  int32_t type;     /* REL_U8, REL_I32 or REL_I64                           */
+  int32_t reserved; /* 0                                                    */
+} rel_col;
+
+/* Row filter term: lo <= col[i] <= hi (inclusive, compared as int64). */
+typedef struct {
+  int32_t col;
+  int32_t reserved;
+  int64_t lo, hi;
+} rel_range_pred;
+
+/* One aggregate.  Its input for row i is
+ *     base[i] * prod_{f < nf} (c[f] + s[f] * fcol[f][i])     (mod 2^64)
+ * with every column read as int64 (u8 zero-, i32 sign-extended).  SUM adds
+ * inputs mod 2^64, MIN / MAX compare them as signed int64, COUNT counts the
+ * group's rows and ignores the input. */
+typedef struct {
+  int32_t op;       /* REL_SUM, REL_COUNT, REL_MIN, REL_MAX                    */
+  int32_t base_col;
+  int32_t nf;       /* 0, 1 or 2                                               */
+  int32_t reserved;
+  int32_t fcol[2];
+  int64_t c[2];
+  int64_t s[2];
+} rel_agg;
+
+/* Filtered group-by:
+ *   rows  : i in [0, n_rows) with every predicate true;
+ *   key   : one key column -> its int64 value; several (u8 / i32 only, at
+ *           most 64 bits together) -> their bit patterns concatenated, the
+ *           first column in the most significant position;
+ *   output: one row per key that has at least one qualifying row. */
+typedef struct {
+  int64_t n_rows;
+  int32_t n_cols, n_keys, n_preds, n_aggs;
+  const rel_col* cols;        /* n_cols   */
+  const int32_t* key_cols;    /* n_keys   */
+  const rel_range_pred* preds;/* n_preds  */
+  const rel_agg* aggs;        /* n_aggs   */
+} rel_groupby_desc;
+
+/* plan flags */
+#define REL_PLAN_EXACT 1u   /* count distinct qualifying keys exactly (GPU pre-pass) */
+#define REL_PLAN_LEARNED 2u /* reserved: sample sketch + learned size / variant      */
+#define REL_PLAN_GENERIC 4u /* force the descriptor-interpreting kernel              */
+
+typedef struct {
+  int64_t slots;            /* global hash-table slots (power of two)           */
+  int32_t variant;          /* REL_VAR_*                                        */
+  int32_t smem_slots;       /* per-CTA table slots: 0 none, 8 thread-private,
+                               16..4096 CTA-shared                              */
+  uint64_t workspace_bytes; /* bytes rel_groupby_agg needs in ws               */
+  uint64_t scratch_bytes;   /* bytes rel_plan_size itself needs in ws          */
+  int64_t est_groups;       /* estimated (or, with REL_PLAN_EXACT, exact)
+                               number of groups                                 */
+  uint32_t flags;           /* REL_PLAN_* used                                  */
+  int32_t reserved;
+} rel_plan;
+
+#define REL_OP_GROUPBY 0
+#define REL_OP_JOIN_PROBE 1
+
+/* Sizing step (the operator's small "decide the next step" kernel, Sec. 2.3).
+ *  op = REL_OP_GROUPBY, desc = const rel_groupby_desc*:
+ *    groups_hint > 0: size the table for that many groups (no GPU work);
+ *    flags & REL_PLAN_EXACT: count distinct qualifying keys on the GPU; needs
+ *      plan->scratch_bytes of ws (query with ws = NULL: returns
+ *      REL_E_CAPACITY after filling scratch_bytes);
+ *    otherwise: size for n_rows groups (always sufficient, rarely economical).
+ *    Fills slots, variant, smem_slots, workspace_bytes, est_groups.
+ *  op = REL_OP_JOIN_PROBE, desc = const rel_join_probe_desc*: counts the
+ *    pairs the probe will emit (the paper's "count" step) into est_groups.
+ *  Returns REL_OK, REL_E_INVALID, REL_E_CAPACITY, REL_E_CUDA, REL_E_TIMEOUT. */
+rel_status rel_plan_size(int32_t op, const void* desc, uint32_t flags, int64_t groups_hint,
+                         void* ws, size_t ws_bytes, rel_plan* plan, void* stream);
+
+/* Run the group-by with a plan from rel_plan_size (plan->variant may be
+ * overridden by the caller; slots must be a power of two >= 16).
+ *  ws       : >= plan->workspace_bytes device bytes, any content on entry;
+ *             the call zeroes what it uses.  Must not be shared by calls that
+ *             overlap on the GPU.
+ *  out_keys : int64[out_capacity] group keys.
+ *  out_aggs : n_aggs device pointers, each int64[out_capacity].
+ *  n_groups_host: receives the number of groups (after a stream sync).
+ * Returns REL_OK; REL_E_CAPACITY when groups > out_capacity (*n_groups_host
+ * = groups; outputs partially written); REL_E_OVERFLOW when the groups did
+ * not fit plan->slots (re-plan larger, e.g. with REL_PLAN_EXACT);
+ * REL_E_INVALID / REL_E_UNSUPPORTED for bad or out-of-limit requests;
+ * REL_E_TIMEOUT, REL_E_CUDA. */
+rel_status rel_groupby_agg(const rel_groupby_desc* desc, const rel_plan* plan, void* ws,
+                           size_t ws_bytes, int64_t* out_keys, int64_t* const* out_aggs,
+                           int64_t out_capacity, int64_t* n_groups_host, void* stream);
+
+/* Device bytes rel_groupby_agg needs for `slots` table slots and `n_aggs`
+ * aggregates. */
+uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs);
+
+/* ----------------------------------------------------------------- join */
+
+/* Handle to a built join table.  It lives in caller memory, points into the
+ * caller's workspace, and stays valid while that workspace is untouched. */
+typedef struct {
+  void* ws;
+  int64_t slots;
+  int64_t n_build;
+  int32_t log2_slots;
+  int32_t magic;
+  uint64_t reserved[4];
+} rel_join_table;
+
+typedef struct {
+  const rel_join_table* table;
+  const int64_t* probe_keys; /* device, n_probe */
+  int64_t n_probe;
+} rel_join_probe_desc;
+
+/* Device bytes rel_join_build needs for n_build build rows. */
+uint64_t rel_join_ws_bytes(int64_t n_build);
+
+/* Build (the paper's insert step): every build row j (key[j], payload[j])
+ * enters an open-addressing table at load factor <= 1/2; duplicate keys are
+ * kept as separate entries.  keys / payload: device int64[n_build];
+ * 0 <= n_build <= 2^31 - 1.  ws >= rel_join_ws_bytes(n_build).  Fills *table.
+ * Returns REL_OK, REL_E_INVALID, REL_E_UNSUPPORTED, REL_E_CUDA, REL_E_OVERFLOW. */
+rel_status rel_join_build(const int64_t* keys, const int64_t* payload, int64_t n_build,
+                          void* ws, size_t ws_bytes, rel_join_table* table, void* stream);
+
+/* Probe (the paper's retrieve step, fused with the payload gather): emits one
+ * row (probe_idx i, build_idx j, payload[j]) for every pair with
+ * probe_keys[i] == key[j] -- the inner-join bag.  Outputs are device arrays of
+ * out_capacity elements.  *n_pairs_host receives the pair count; REL_E_CAPACITY
+ * when it exceeds out_capacity (outputs then hold an unspecified subset).
+ * Probes on one table must not overlap on the GPU (they share a cursor). */
+rel_status rel_join_probe(const rel_join_table* table, const int64_t* probe_keys,
+                          int64_t n_probe, int32_t* out_probe_idx, int32_t* out_build_idx,
+                          int64_t* out_payload, int64_t out_capacity, int64_t* n_pairs_host,
+                          void* stream);
+
+/* ---------------------------------------------------------- diagnostics */
+
+/* Thread-local message for the last non-OK status on this thread. */
+const char* rel_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t rel_launch_count(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int32_t rel_version(void);
+
+/* Kernel timing for measurement.  rel_profile_start() clears the record and
+ * makes every later kernel launch of this library record a CUDA event pair on
+ * its own stream; rel_profile_stop() waits for those events, writes up to
+ * `max` records in launch order (kernel id, milliseconds) and returns the
+ * number of records taken (possibly > max), or -1 on a CUDA error.  Host
+ * only; not thread-safe against concurrent launches from other threads. */
+void rel_profile_start(void);
+int64_t rel_profile_stop(int32_t* kernel_ids, float* ms, int64_t max);
+
+/* Name of a kernel id reported by rel_profile_stop ("?" if unknown). */
+const char* rel_kernel_name(int32_t kernel_id);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REL_H */

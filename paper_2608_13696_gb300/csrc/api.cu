@@ -1,0 +1,606 @@
+// C-ABI entry points (include/rel.h): argument validation, planning, the
+// mapping of a descriptor onto a specialised kernel, and the launches.
+// Validation happens before any CUDA call, so a rejected request never
+// touches the device.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "groupby.cuh"
+#include "join.cuh"
+
+// ------------------------------------------------------------ host helpers
+
+namespace relhost {
+
+static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+rel_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return REL_E_CUDA;
+}
+
+void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Event timing of launches (rel_profile_start / rel_profile_stop).
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;      // records of the current window
+static std::vector<cudaEvent_t> g_pool;  // events reused across windows
+static size_t g_pool_used = 0;
+
+static cudaEvent_t pool_event() {
+  if (g_pool_used == g_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g_pool.push_back(e);
+  }
+  return g_pool[g_pool_used++];
+}
+
+void launch_begin(int id, cudaStream_t st) {
+  count_launch(1);
+  if (!g_prof_on) return;
+  ProfRec r{id, pool_event(), pool_event()};
+  if (!r.a || !r.b) return;
+  cudaEventRecord(r.a, st);
+  g_prof.push_back(r);
+}
+
+void launch_end(int id, cudaStream_t st) {
+  if (!g_prof_on || g_prof.empty() || g_prof.back().id != id) return;
+  cudaEventRecord(g_prof.back().b, st);
+}
+
+int device_sms() {
+  static int cache[128] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 148;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+}  // namespace relhost
+
+using relhost::set_error;
+
+namespace {
+
+using namespace rel;
+
+constexpr int32_t TABLE_MAGIC = 0x4a4f494e;  // "JOIN"
+constexpr int64_t MAX_INDEX_ROWS = 2147483647;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+int elem_size(int32_t t) { return t == REL_U8 ? 1 : t == REL_I32 ? 4 : 8; }
+int elem_bits(int32_t t) { return 8 * elem_size(t); }
+bool valid_type(int32_t t) { return t == REL_U8 || t == REL_I32 || t == REL_I64; }
+
+int log2_pow2(uint64_t x) {
+  int l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+rel_status validate_desc(const rel_groupby_desc* d) {
+  if (!d) return set_error("group-by: NULL descriptor"), REL_E_INVALID;
+  if (d->n_rows < 0) return set_error("group-by: n_rows < 0"), REL_E_INVALID;
+  if (d->n_cols < 1 || d->n_cols > REL_MAX_COLS || !d->cols)
+    return set_error("group-by: n_cols must be 1..%d", REL_MAX_COLS), REL_E_INVALID;
+  for (int c = 0; c < d->n_cols; ++c) {
+    if (!valid_type(d->cols[c].type))
+      return set_error("group-by: column %d has an unknown type", c), REL_E_INVALID;
+    if (d->n_rows > 0 && !d->cols[c].data)
+      return set_error("group-by: column %d has no data", c), REL_E_INVALID;
+    if ((uintptr_t)d->cols[c].data % elem_size(d->cols[c].type))
+      return set_error("group-by: column %d is not aligned to its element", c), REL_E_INVALID;
+  }
+  auto col_ok = [&](int32_t c) { return c >= 0 && c < d->n_cols; };
+  if (d->n_keys < 1 || d->n_keys > REL_MAX_KEYS || !d->key_cols)
+    return set_error("group-by: n_keys must be 1..%d", REL_MAX_KEYS), REL_E_INVALID;
+  int bits = 0;
+  for (int k = 0; k < d->n_keys; ++k) {
+    if (!col_ok(d->key_cols[k])) return set_error("group-by: bad key column"), REL_E_INVALID;
+    int32_t t = d->cols[d->key_cols[k]].type;
+    if (d->n_keys > 1 && t == REL_I64)
+      return set_error("group-by: a packed key may not contain an int64 column"), REL_E_INVALID;
+    bits += elem_bits(t);
+  }
+  if (d->n_keys > 1 && bits > 64)
+    return set_error("group-by: packed key wider than 64 bits"), REL_E_INVALID;
+  if (d->n_preds < 0 || d->n_preds > REL_MAX_PREDS || (d->n_preds && !d->preds))
+    return set_error("group-by: n_preds must be 0..%d", REL_MAX_PREDS), REL_E_INVALID;
+  for (int i = 0; i < d->n_preds; ++i)
+    if (!col_ok(d->preds[i].col)) return set_error("group-by: bad predicate column"), REL_E_INVALID;
+  if (d->n_aggs < 1 || d->n_aggs > REL_MAX_AGGS || !d->aggs)
+    return set_error("group-by: n_aggs must be 1..%d", REL_MAX_AGGS), REL_E_INVALID;
+  for (int a = 0; a < d->n_aggs; ++a) {
+    const rel_agg& g = d->aggs[a];
+    if (g.op < REL_SUM || g.op > REL_MAX) return set_error("group-by: bad aggregate op"), REL_E_INVALID;
+    if (g.op == REL_COUNT) continue;
+    if (!col_ok(g.base_col)) return set_error("group-by: bad aggregate column"), REL_E_INVALID;
+    if (g.nf < 0 || g.nf > 2) return set_error("group-by: nf must be 0..2"), REL_E_INVALID;
+    for (int f = 0; f < g.nf; ++f)
+      if (!col_ok(g.fcol[f])) return set_error("group-by: bad factor column"), REL_E_INVALID;
+  }
+  return REL_OK;
+}
+
+// Which specialised kernel (if any) computes this descriptor.
+int match_shape(const rel_groupby_desc* d, GbParams& p) {
+  auto T = [&](int c) { return d->cols[c].type; };
+  // key column + one int64 value column, no filter, no factors
+  if (d->n_keys == 1 && d->n_preds == 0 && d->n_aggs <= 4 &&
+      (T(d->key_cols[0]) == REL_I64 || T(d->key_cols[0]) == REL_I32)) {
+    int vcol = -1;
+    bool ok = true;
+    for (int a = 0; a < d->n_aggs && ok; ++a) {
+      const rel_agg& g = d->aggs[a];
+      if (g.op == REL_COUNT) continue;
+      if (g.nf != 0 || T(g.base_col) != REL_I64) ok = false;
+      else if (vcol < 0) vcol = g.base_col;
+      else if (vcol != g.base_col) ok = false;
+    }
+    if (ok) {
+      p.r_a = vcol < 0 ? d->key_cols[0] : vcol;
+      if (vcol < 0 && T(p.r_a) != REL_I64) return SHAPE_GENERIC;
+      return T(d->key_cols[0]) == REL_I64 ? SHAPE_KV64 : SHAPE_KV32;
+    }
+  }
+  // (u8, u8) key, one int32 range filter, five aggregates of the form
+  // sum(a), sum(b), sum(b*f0(d)), sum(b*f0(d)*f1(t)), count over int64 columns
+  if (d->n_keys == 2 && T(d->key_cols[0]) == REL_U8 && T(d->key_cols[1]) == REL_U8 &&
+      d->n_preds == 1 && T(d->preds[0].col) == REL_I32 && d->n_aggs == 5) {
+    const rel_agg* g = d->aggs;
+    auto i64 = [&](int c) { return T(c) == REL_I64; };
+    bool ok = g[0].op == REL_SUM && g[0].nf == 0 && i64(g[0].base_col) &&
+              g[1].op == REL_SUM && g[1].nf == 0 && i64(g[1].base_col) &&
+              g[2].op == REL_SUM && g[2].nf == 1 && g[2].base_col == g[1].base_col &&
+              i64(g[2].fcol[0]) && g[3].op == REL_SUM && g[3].nf == 2 &&
+              g[3].base_col == g[1].base_col && g[3].fcol[0] == g[2].fcol[0] &&
+              g[3].c[0] == g[2].c[0] && g[3].s[0] == g[2].s[0] && i64(g[3].fcol[1]) &&
+              g[4].op == REL_COUNT;
+    if (ok) {
+      p.r_k0 = d->key_cols[0];
+      p.r_k1 = d->key_cols[1];
+      p.r_pred = d->preds[0].col;
+      p.r_a = g[0].base_col;
+      p.r_b = g[1].base_col;
+      p.r_d = g[2].fcol[0];
+      p.r_t = g[3].fcol[1];
+      return SHAPE_Q1;
+    }
+  }
+  return SHAPE_GENERIC;
+}
+
+void fill_params(const rel_groupby_desc* d, GbParams& p) {
+  std::memset(&p, 0, sizeof p);
+  p.n_rows = d->n_rows;
+  p.n_cols = d->n_cols;
+  p.n_keys = d->n_keys;
+  p.n_preds = d->n_preds;
+  p.n_aggs = d->n_aggs;
+  for (int c = 0; c < d->n_cols; ++c) {
+    p.col[c] = (const uint8_t*)d->cols[c].data;
+    p.ctype[c] = d->cols[c].type;
+    p.csize[c] = elem_size(d->cols[c].type);
+  }
+  int shift = 0;
+  for (int k = d->n_keys - 1; k >= 0; --k) {
+    const int w = elem_bits(d->cols[d->key_cols[k]].type);
+    p.key_col[k] = d->key_cols[k];
+    p.key_shift[k] = d->n_keys == 1 ? 0 : shift;
+    p.key_mask[k] = w >= 64 ? ~0ull : ((1ull << w) - 1);
+    shift += w;
+  }
+  for (int i = 0; i < d->n_preds; ++i) {
+    p.pred_col[i] = d->preds[i].col;
+    p.pred_lo[i] = d->preds[i].lo;
+    p.pred_hi[i] = d->preds[i].hi;
+  }
+  for (int a = 0; a < d->n_aggs; ++a) {
+    const rel_agg& g = d->aggs[a];
+    p.aop[a] = g.op;
+    p.abase[a] = g.op == REL_COUNT ? 0 : g.base_col;
+    p.anf[a] = g.op == REL_COUNT ? 0 : g.nf;
+    for (int f = 0; f < 2; ++f) {
+      p.afcol[a][f] = f < p.anf[a] ? g.fcol[f] : 0;
+      p.ac[a][f] = g.c[f];
+      p.as[a][f] = g.s[f];
+    }
+    if (agg_kind(g.op) == KIND_UMAX) p.umax_mask |= 1u << a;
+  }
+}
+
+// Rows per tile so that the staging ring fits next to the backend's table.
+int choose_tile(const GbParams& p, uint64_t be_bytes, int mode) {
+  uint64_t row_bytes = 0;
+  for (int c = 0; c < p.n_cols; ++c) row_bytes += (uint64_t)p.csize[c];
+  const uint64_t budget = SMEM_LIMIT - 256 - ((be_bytes + 127) & ~127ull);
+  const uint64_t target = mode == MODE_GLOBAL || mode == MODE_KEYSET ? 16384 : 65536;
+  int t = 4096;
+  while (t > 256 && ((uint64_t)t * row_bytes > target || (uint64_t)GB_STAGES * t * row_bytes > budget))
+    t >>= 1;
+  if ((uint64_t)GB_STAGES * t * row_bytes > budget) return 0;
+  return t;
+}
+
+void set_stages(GbParams& p, int tile) {
+  p.tile_rows = tile;
+  uint32_t off = 0;
+  for (int c = 0; c < p.n_cols; ++c) {
+    p.stage_off[c] = off;
+    off += (uint32_t)(tile * p.csize[c]);  // multiple of 16: tile % 16 == 0
+  }
+  p.stage_bytes = off;
+}
+
+bool tma_ok(const GbParams& p) {
+  for (int c = 0; c < p.n_cols; ++c)
+    if ((uintptr_t)p.col[c] % 16) return false;
+  return true;
+}
+
+struct HostHeader {
+  unsigned long long n_out, n_side;
+  unsigned int overflow, timeout;
+  unsigned long long aux;
+};
+
+rel_status read_header(const void* ws, HostHeader* h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h, ws, sizeof(HostHeader), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "reading the status header");
+}
+
+// Launch the fused kernel for one mode, degrading to smaller per-CTA tables
+// when the requested one does not fit in shared memory.
+rel_status run_main(GbParams& p, int shape, int mode, bool generic_only, cudaStream_t st) {
+  if (generic_only) shape = SHAPE_GENERIC;
+  for (;;) {
+    const uint64_t be = gb_backend_smem_bytes(mode, shape, p.smem_slots);
+    const int tile = choose_tile(p, be, mode);
+    if (tile > 0) {
+      set_stages(p, tile);
+      return gb_launch_main(p, shape, mode, tma_ok(p), st);
+    }
+    if (mode == MODE_TINY) {
+      mode = MODE_SHARED;
+      p.smem_slots = 256;
+    } else if ((mode == MODE_SHARED || mode == MODE_KEYSET) && p.smem_slots > 16) {
+      p.smem_slots >>= 1;
+    } else if (mode == MODE_SHARED) {
+      mode = MODE_GLOBAL;
+      p.smem_slots = 0;
+    } else {
+      set_error("group-by: rows too wide to stage");
+      return REL_E_UNSUPPORTED;
+    }
+  }
+}
+
+uint64_t gb_ws_bytes(int64_t slots, int32_t n_aggs) {
+  return HEADER_BYTES + (uint64_t)slots * 8ull * (1ull + (uint64_t)n_aggs);
+}
+
+void choose_variant(int64_t est, int n_aggs, rel_plan* plan) {
+  if (est <= 6 && n_aggs <= 6) {
+    plan->variant = REL_VAR_SMEM;
+    plan->smem_slots = TINY_SLOTS;
+  } else if (est <= 2048) {
+    plan->variant = REL_VAR_SMEM;
+    plan->smem_slots = (int32_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
+    if (plan->smem_slots > 4096) plan->smem_slots = 4096;
+  } else {
+    plan->variant = REL_VAR_GLOBAL;
+    plan->smem_slots = 0;
+  }
+}
+
+rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint, void* ws,
+                        size_t ws_bytes, rel_plan* plan, cudaStream_t st) {
+  rel_status r = validate_desc(d);
+  if (r) return r;
+  std::memset(plan, 0, sizeof *plan);
+  plan->flags = flags;
+  int64_t est;
+  if (hint > 0) {
+    est = hint;
+  } else if (flags & REL_PLAN_EXACT) {
+    const uint64_t set_slots = next_pow2((uint64_t)(2 * d->n_rows < 16 ? 16 : 2 * d->n_rows));
+    plan->scratch_bytes = HEADER_BYTES + 8ull * set_slots;
+    if (!ws || ws_bytes < plan->scratch_bytes) {
+      set_error("plan: exact sizing needs %llu workspace bytes",
+                (unsigned long long)plan->scratch_bytes);
+      return REL_E_CAPACITY;
+    }
+    if (d->n_rows == 0) {
+      est = 0;
+    } else {
+      GbParams p;
+      fill_params(d, p);
+      const int shape = match_shape(d, p);
+      p.hdr = (WsHeader*)ws;
+      p.tkeys = (uint64_t*)((uint8_t*)ws + HEADER_BYTES);
+      p.log2_slots = log2_pow2(set_slots);
+      p.max_probe = (uint32_t)(set_slots < 4096 ? set_slots : 4096);
+      p.smem_slots = 1024;
+      cudaError_t e = cudaMemsetAsync(ws, 0, plan->scratch_bytes, st);
+      if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+      r = run_main(p, shape, MODE_KEYSET, (flags & REL_PLAN_GENERIC) != 0, st);
+      if (r) return r;
+      HostHeader h;
+      if ((r = read_header(ws, &h, st))) return r;
+      if (h.timeout) return set_error("plan: a device wait timed out"), REL_E_TIMEOUT;
+      if (h.overflow) return set_error("plan: key set overflow"), REL_E_OVERFLOW;
+      est = (int64_t)h.aux + (h.n_side > 0 ? 1 : 0);
+    }
+  } else {
+    est = d->n_rows;
+  }
+  plan->est_groups = est;
+  plan->slots = (int64_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
+  choose_variant(est, d->n_aggs, plan);
+  plan->workspace_bytes = gb_ws_bytes(plan->slots, d->n_aggs);
+  return REL_OK;
+}
+
+// ------------------------------------------------------------------ join
+
+struct JoinLayout {
+  uint64_t slots;
+  uint64_t bytes;
+};
+
+JoinLayout join_layout(int64_t n_build) {
+  JoinLayout L;
+  L.slots = next_pow2((uint64_t)(2 * n_build < 16 ? 16 : 2 * n_build));
+  L.bytes = HEADER_BYTES + L.slots * (8 + sizeof(JoinVal)) +
+            (uint64_t)(n_build > 0 ? n_build : 1) * sizeof(JoinVal);
+  return L;
+}
+
+JoinParams join_params(const rel_join_table* t) {
+  JoinParams p;
+  uint8_t* ws = (uint8_t*)t->ws;
+  const uint64_t slots = (uint64_t)t->slots;
+  p.hdr = (WsHeader*)ws;
+  p.tkeys = (uint64_t*)(ws + HEADER_BYTES);
+  p.tvals = (JoinVal*)(ws + HEADER_BYTES + 8 * slots);
+  p.side = (JoinVal*)(ws + HEADER_BYTES + (8 + sizeof(JoinVal)) * slots);
+  p.log2_slots = t->log2_slots;
+  return p;
+}
+
+rel_status validate_table(const rel_join_table* t) {
+  if (!t || t->magic != TABLE_MAGIC || !t->ws || !is_pow2((uint64_t)t->slots))
+    return set_error("join: not a built table"), REL_E_INVALID;
+  return REL_OK;
+}
+
+rel_status count_pairs(const rel_join_probe_desc* pd, int64_t* out, cudaStream_t st) {
+  if (!pd) return set_error("join: NULL probe descriptor"), REL_E_INVALID;
+  rel_status r = validate_table(pd->table);
+  if (r) return r;
+  if (pd->n_probe < 0 || pd->n_probe > MAX_INDEX_ROWS)
+    return set_error("join: n_probe outside [0, 2^31-1]"), REL_E_UNSUPPORTED;
+  if (pd->n_probe > 0 && !pd->probe_keys) return set_error("join: no probe keys"), REL_E_INVALID;
+  JoinParams p = join_params(pd->table);
+  cudaError_t e = cudaMemsetAsync(&p.hdr->aux, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+  JoinOut o{nullptr, nullptr, nullptr, 0};
+  if ((r = join_launch_probe(p, o, pd->probe_keys, pd->n_probe, false, st))) return r;
+  HostHeader h;
+  if ((r = read_header(p.hdr, &h, st))) return r;
+  *out = (int64_t)h.aux;
+  return REL_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char* rel_last_error(void) { return relhost::g_err; }
+
+uint64_t rel_launch_count(void) { return relhost::g_launches.load(); }
+
+int32_t rel_version(void) { return 100; }
+
+void rel_profile_start(void) {
+  relhost::g_prof.clear();
+  relhost::g_pool_used = 0;
+  relhost::g_prof_on = true;
+}
+
+int64_t rel_profile_stop(int32_t* ids, float* ms, int64_t max) {
+  relhost::g_prof_on = false;
+  int64_t n = 0;
+  for (const auto& r : relhost::g_prof) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return -1;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return -1;
+    if (n < max) {
+      if (ids) ids[n] = r.id;
+      if (ms) ms[n] = t;
+    }
+    ++n;
+  }
+  return n;
+}
+
+const char* rel_kernel_name(int32_t id) {
+  static const char* names[] = {"gb_main_global", "gb_main_tiny", "gb_main_shared",
+                                "gb_main_keyset", "gb_compact", "join_build",
+                                "join_probe", "join_count"};
+  return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
+}
+
+uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs) {
+  if (slots < 0 || n_aggs < 0) return 0;
+  return gb_ws_bytes(slots, n_aggs);
+}
+
+uint64_t rel_join_ws_bytes(int64_t n_build) {
+  if (n_build < 0) return 0;
+  return join_layout(n_build).bytes;
+}
+
+rel_status rel_plan_size(int32_t op, const void* desc, uint32_t flags, int64_t groups_hint,
+                         void* ws, size_t ws_bytes, rel_plan* plan, void* stream) {
+  if (!plan) return set_error("plan: NULL plan"), REL_E_INVALID;
+  if (op == REL_OP_GROUPBY)
+    return plan_groupby((const rel_groupby_desc*)desc, flags, groups_hint, ws, ws_bytes, plan,
+                        as_stream(stream));
+  if (op == REL_OP_JOIN_PROBE) {
+    std::memset(plan, 0, sizeof *plan);
+    plan->flags = flags;
+    int64_t n = 0;
+    rel_status r = count_pairs((const rel_join_probe_desc*)desc, &n, as_stream(stream));
+    if (r) return r;
+    plan->est_groups = n;
+    return REL_OK;
+  }
+  set_error("plan: unknown op %d", op);
+  return REL_E_INVALID;
+}
+
+rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void* ws,
+                           size_t ws_bytes, int64_t* out_keys, int64_t* const* out_aggs,
+                           int64_t out_capacity, int64_t* n_groups_host, void* stream) {
+  rel_status r = validate_desc(d);
+  if (r) return r;
+  if (!plan) return set_error("group-by: NULL plan"), REL_E_INVALID;
+  if (plan->slots < 16 || !is_pow2((uint64_t)plan->slots))
+    return set_error("group-by: plan slots must be a power of two >= 16"), REL_E_INVALID;
+  const int32_t ss = plan->smem_slots;
+  if (!(ss == 0 || ss == TINY_SLOTS || (ss >= 16 && ss <= 4096 && is_pow2((uint64_t)ss))))
+    return set_error("group-by: smem_slots must be 0, 8 or a power of two in [16, 4096]"),
+           REL_E_INVALID;
+  const uint64_t need = gb_ws_bytes(plan->slots, d->n_aggs);
+  if (!ws || ws_bytes < need) {
+    set_error("group-by: workspace needs %llu bytes", (unsigned long long)need);
+    return REL_E_CAPACITY;
+  }
+  if (out_capacity < 0 || (out_capacity > 0 && (!out_keys || !out_aggs)))
+    return set_error("group-by: bad outputs"), REL_E_INVALID;
+  GbOut o;
+  std::memset(&o, 0, sizeof o);
+  o.keys = out_keys;
+  o.capacity = out_capacity;
+  for (int a = 0; a < d->n_aggs; ++a) {
+    o.aggs[a] = out_capacity > 0 ? out_aggs[a] : nullptr;
+    if (out_capacity > 0 && !o.aggs[a]) return set_error("group-by: NULL aggregate output"), REL_E_INVALID;
+  }
+  cudaStream_t st = as_stream(stream);
+  GbParams p;
+  fill_params(d, p);
+  const int shape = match_shape(d, p);
+  p.hdr = (WsHeader*)ws;
+  p.tkeys = (uint64_t*)((uint8_t*)ws + HEADER_BYTES);
+  p.taggs = (unsigned long long*)(p.tkeys + plan->slots);
+  p.log2_slots = log2_pow2((uint64_t)plan->slots);
+  p.max_probe = (uint32_t)(plan->slots < 4096 ? plan->slots : 4096);
+  p.smem_slots = (uint32_t)(ss >= 16 ? ss : 0);
+  const int mode = ss == TINY_SLOTS ? MODE_TINY : ss >= 16 ? MODE_SHARED : MODE_GLOBAL;
+  cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+  if ((r = run_main(p, shape, mode, (plan->flags & REL_PLAN_GENERIC) != 0, st))) return r;
+  if ((r = gb_launch_compact(p, o, st))) return r;
+  if (!n_groups_host) return REL_OK;
+  HostHeader h;
+  if ((r = read_header(ws, &h, st))) return r;
+  *n_groups_host = (int64_t)h.n_out;
+  if (h.timeout) return set_error("group-by: a device wait timed out"), REL_E_TIMEOUT;
+  if (h.overflow) {
+    *n_groups_host = -1;
+    return set_error("group-by: more groups than the plan's %lld slots hold",
+                     (long long)plan->slots),
+           REL_E_OVERFLOW;
+  }
+  if ((int64_t)h.n_out > out_capacity)
+    return set_error("group-by: %llu groups exceed the output capacity", h.n_out), REL_E_CAPACITY;
+  return REL_OK;
+}
+
+rel_status rel_join_build(const int64_t* keys, const int64_t* payload, int64_t n_build, void* ws,
+                          size_t ws_bytes, rel_join_table* table, void* stream) {
+  if (!table) return set_error("join: NULL table handle"), REL_E_INVALID;
+  if (n_build < 0 || n_build > MAX_INDEX_ROWS)
+    return set_error("join: n_build outside [0, 2^31-1]"), REL_E_UNSUPPORTED;
+  if (n_build > 0 && (!keys || !payload)) return set_error("join: no build columns"), REL_E_INVALID;
+  const JoinLayout L = join_layout(n_build);
+  if (!ws || ws_bytes < L.bytes) {
+    set_error("join: workspace needs %llu bytes", (unsigned long long)L.bytes);
+    return REL_E_CAPACITY;
+  }
+  std::memset(table, 0, sizeof *table);
+  table->ws = ws;
+  table->slots = (int64_t)L.slots;
+  table->n_build = n_build;
+  table->log2_slots = log2_pow2(L.slots);
+  table->magic = TABLE_MAGIC;
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + 8 * L.slots, st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+  return join_launch_build(join_params(table), keys, payload, n_build, st);
+}
+
+rel_status rel_join_probe(const rel_join_table* t, const int64_t* probe_keys, int64_t n_probe,
+                          int32_t* out_probe_idx, int32_t* out_build_idx, int64_t* out_payload,
+                          int64_t out_capacity, int64_t* n_pairs_host, void* stream) {
+  rel_status r = validate_table(t);
+  if (r) return r;
+  if (n_probe < 0 || n_probe > MAX_INDEX_ROWS)
+    return set_error("join: n_probe outside [0, 2^31-1]"), REL_E_UNSUPPORTED;
+  if (n_probe > 0 && !probe_keys) return set_error("join: no probe keys"), REL_E_INVALID;
+  if (out_capacity < 0 ||
+      (out_capacity > 0 && (!out_probe_idx || !out_build_idx || !out_payload)))
+    return set_error("join: bad outputs"), REL_E_INVALID;
+  cudaStream_t st = as_stream(stream);
+  JoinParams p = join_params(t);
+  cudaError_t e = cudaMemsetAsync(&p.hdr->n_out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+  JoinOut o{out_probe_idx, out_build_idx, out_payload, out_capacity};
+  if ((r = join_launch_probe(p, o, probe_keys, n_probe, true, st))) return r;
+  if (!n_pairs_host) return REL_OK;
+  HostHeader h;
+  if ((r = read_header(p.hdr, &h, st))) return r;
+  *n_pairs_host = (int64_t)h.n_out;
+  if (h.overflow) return set_error("join: build table overflow"), REL_E_OVERFLOW;
+  if ((int64_t)h.n_out > out_capacity)
+    return set_error("join: %llu pairs exceed the output capacity", h.n_out), REL_E_CAPACITY;
+  return REL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,298 @@
+"""Thin ctypes binding over librel.so (include/rel.h).
+
+Argument marshalling only: every step of the group-by and join runs in the
+library's CUDA kernels.  torch supplies device memory (the caching allocator)
+and the current stream.  There is no CPU fallback: without the compiled
+library and a CUDA device every call raises.
+
+Query descriptions are dicts:
+    cols  : list of CUDA tensors (torch.uint8, torch.int32 or torch.int64), equal length
+    keys  : list of column indices
+    preds : list of (col, lo, hi), inclusive
+    aggs  : list of (op, base_col, [(fcol, c, s), ...]); op in sum/count/min/max
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+REL_OK, REL_E_INVALID, REL_E_CAPACITY, REL_E_CUDA = 0, -1, -2, -3
+REL_E_TIMEOUT, REL_E_UNSUPPORTED, REL_E_OVERFLOW = -4, -5, -6
+STATUS_NAMES = {0: "REL_OK", -1: "REL_E_INVALID", -2: "REL_E_CAPACITY", -3: "REL_E_CUDA",
+                -4: "REL_E_TIMEOUT", -5: "REL_E_UNSUPPORTED", -6: "REL_E_OVERFLOW"}
+U8, I32, I64 = 0, 1, 2
+OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
+VAR_AUTO, VAR_SMEM, VAR_GLOBAL, VAR_PARTITIONED = 0, 1, 2, 3
+PLAN_EXACT, PLAN_LEARNED, PLAN_GENERIC = 1, 2, 4
+OP_GROUPBY, OP_JOIN_PROBE = 0, 1
+MAX_COLS, MAX_KEYS, MAX_PREDS, MAX_AGGS = 8, 4, 4, 8
+
+_DT = {torch.uint8: U8, torch.int32: I32, torch.int64: I64}
+
+
+class RelError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Col(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("type", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RangePred(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("reserved", ctypes.c_int32), ("lo", ctypes.c_int64),
+                ("hi", ctypes.c_int64)]
+
+
+class Agg(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("base_col", ctypes.c_int32), ("nf", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("fcol", ctypes.c_int32 * 2),
+                ("c", ctypes.c_int64 * 2), ("s", ctypes.c_int64 * 2)]
+
+
+class GroupByDesc(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int32),
+                ("n_keys", ctypes.c_int32), ("n_preds", ctypes.c_int32),
+                ("n_aggs", ctypes.c_int32), ("cols", ctypes.POINTER(Col)),
+                ("key_cols", ctypes.POINTER(ctypes.c_int32)),
+                ("preds", ctypes.POINTER(RangePred)), ("aggs", ctypes.POINTER(Agg))]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int64), ("variant", ctypes.c_int32),
+                ("smem_slots", ctypes.c_int32), ("workspace_bytes", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_uint64), ("est_groups", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+    def __repr__(self):
+        return (f"Plan(slots={self.slots}, variant={self.variant}, smem_slots={self.smem_slots}, "
+                f"workspace_bytes={self.workspace_bytes}, est_groups={self.est_groups})")
+
+
+class JoinTableC(ctypes.Structure):
+    _fields_ = [("ws", ctypes.c_void_p), ("slots", ctypes.c_int64), ("n_build", ctypes.c_int64),
+                ("log2_slots", ctypes.c_int32), ("magic", ctypes.c_int32),
+                ("reserved", ctypes.c_uint64 * 4)]
+
+
+class JoinProbeDesc(ctypes.Structure):
+    _fields_ = [("table", ctypes.POINTER(JoinTableC)), ("probe_keys", ctypes.c_void_p),
+                ("n_probe", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# every function include/rel.h declares (the ABI test checks the header agrees)
+EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join_ws_bytes",
+           "rel_join_build", "rel_join_probe", "rel_last_error", "rel_launch_count",
+           "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load librel.so (building it first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_stale and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"librel.so is missing ({_build.LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, u32, u64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_uint32, ctypes.c_uint64)
+        L.rel_plan_size.restype = i32
+        L.rel_plan_size.argtypes = [i32, vp, u32, i64, vp, ctypes.c_size_t, ctypes.POINTER(Plan), vp]
+        L.rel_groupby_agg.restype = i32
+        L.rel_groupby_agg.argtypes = [ctypes.POINTER(GroupByDesc), ctypes.POINTER(Plan), vp,
+                                      ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_void_p), i64,
+                                      ctypes.POINTER(i64), vp]
+        L.rel_groupby_ws_bytes.restype = u64
+        L.rel_groupby_ws_bytes.argtypes = [i64, i32]
+        L.rel_join_ws_bytes.restype = u64
+        L.rel_join_ws_bytes.argtypes = [i64]
+        L.rel_join_build.restype = i32
+        L.rel_join_build.argtypes = [vp, vp, i64, vp, ctypes.c_size_t, ctypes.POINTER(JoinTableC), vp]
+        L.rel_join_probe.restype = i32
+        L.rel_join_probe.argtypes = [ctypes.POINTER(JoinTableC), vp, i64, vp, vp, vp, i64,
+                                     ctypes.POINTER(i64), vp]
+        L.rel_last_error.restype = ctypes.c_char_p
+        L.rel_last_error.argtypes = []
+        L.rel_launch_count.restype = u64
+        L.rel_launch_count.argtypes = []
+        L.rel_version.restype = i32
+        L.rel_version.argtypes = []
+        L.rel_profile_start.restype = None
+        L.rel_profile_start.argtypes = []
+        L.rel_profile_stop.restype = i64
+        L.rel_profile_stop.argtypes = [vp, vp, i64]
+        L.rel_kernel_name.restype = ctypes.c_char_p
+        L.rel_kernel_name.argtypes = [i32]
+        _lib = L
+        return L
+
+
+def _check(status: int, allow=()) -> int:
+    if status != REL_OK and status not in allow:
+        raise RelError(status, load().rel_last_error().decode())
+    return status
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def launch_count() -> int:
+    return int(load().rel_launch_count())
+
+
+def profile_start() -> None:
+    """Record a CUDA event pair around every later library launch."""
+    load().rel_profile_start()
+
+
+def profile_stop():
+    """Stop recording; returns [(kernel name, milliseconds), ...] in launch order."""
+    L = load()
+    n = L.rel_profile_stop(None, None, 0)
+    if n < 0:
+        raise RelError(REL_E_CUDA, "profile events")
+    ids = (ctypes.c_int32 * max(1, n))()
+    ms = (ctypes.c_float * max(1, n))()
+    L.rel_profile_stop(ids, ms, n)
+    return [(L.rel_kernel_name(ids[i]).decode(), float(ms[i])) for i in range(n)]
+
+
+class _Desc:
+    """Keeps the ctypes arrays of one descriptor alive."""
+
+    def __init__(self, q: dict):
+        cols = q["cols"]
+        if not cols:
+            raise ValueError("no columns")
+        n = cols[0].numel()
+        for c in cols:
+            if c.dtype not in _DT or c.numel() != n or not c.is_cuda or not c.is_contiguous():
+                raise ValueError("columns must be contiguous CUDA uint8/int32/int64 of one length")
+        self.tensors = cols
+        self.cols = (Col * len(cols))(*[Col(c.data_ptr(), _DT[c.dtype], 0) for c in cols])
+        self.keys = (ctypes.c_int32 * max(1, len(q["keys"])))(*q["keys"])
+        preds = q.get("preds", [])
+        self.preds = (RangePred * max(1, len(preds)))(*[RangePred(c, 0, lo, hi) for c, lo, hi in preds])
+        aggs = []
+        for op, base, fs in q["aggs"]:
+            a = Agg(OPS[op], base, len(fs), 0)
+            for f, (fc, c, s) in enumerate(fs):
+                a.fcol[f], a.c[f], a.s[f] = fc, c, s
+            aggs.append(a)
+        self.aggs = (Agg * max(1, len(aggs)))(*aggs)
+        self.n_aggs = len(aggs)
+        self.d = GroupByDesc(n, len(cols), len(q["keys"]), len(preds), len(aggs), self.cols,
+                             self.keys, self.preds, self.aggs)
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def plan_groupby(q: dict, flags: int = 0, groups_hint: int = 0, stream=None) -> Plan:
+    """rel_plan_size for a group-by (REL_PLAN_EXACT runs the GPU distinct count)."""
+    L = load()
+    d = _Desc(q)
+    plan = Plan()
+    dev = q["cols"][0].device
+    st = _stream(stream)
+    r = L.rel_plan_size(OP_GROUPBY, ctypes.byref(d.d), flags, groups_hint, None, 0,
+                        ctypes.byref(plan), st)
+    if r == REL_E_CAPACITY and plan.scratch_bytes:
+        ws = _ws(plan.scratch_bytes, dev)
+        r = L.rel_plan_size(OP_GROUPBY, ctypes.byref(d.d), flags, groups_hint, ws.data_ptr(),
+                            ws.numel(), ctypes.byref(plan), st)
+    _check(r)
+    return plan
+
+
+def groupby(q: dict, plan: Plan | None = None, flags: int = 0, groups_hint: int = 0,
+            capacity: int | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Run the fused filter + group-by.  Returns (keys int64[G], [agg int64[G], ...])
+    in unspecified group order."""
+    L = load()
+    d = _Desc(q)
+    dev = q["cols"][0].device
+    if plan is None:
+        plan = plan_groupby(q, flags=flags, groups_hint=groups_hint, stream=stream)
+    if capacity is None:
+        capacity = max(1, plan.est_groups + 1)
+    if ws is None or ws.numel() < plan.workspace_bytes:
+        ws = _ws(plan.workspace_bytes, dev)
+    st = _stream(stream)
+    while True:
+        keys = torch.empty(capacity, dtype=torch.int64, device=dev)
+        aggs = [torch.empty(capacity, dtype=torch.int64, device=dev) for _ in range(d.n_aggs)]
+        ptrs = (ctypes.c_void_p * max(1, d.n_aggs))(*[a.data_ptr() for a in aggs])
+        n = ctypes.c_int64(0)
+        r = L.rel_groupby_agg(ctypes.byref(d.d), ctypes.byref(plan), ws.data_ptr(), ws.numel(),
+                              keys.data_ptr(), ptrs, capacity, ctypes.byref(n), st)
+        if r == REL_E_CAPACITY and n.value > capacity:
+            capacity = n.value
+            continue
+        _check(r)
+        g = n.value
+        return keys[:g], [a[:g] for a in aggs]
+
+
+class JoinTable:
+    """A built join table; owns its workspace tensor."""
+
+    def __init__(self, keys: torch.Tensor, payload: torch.Tensor, stream=None):
+        L = load()
+        if keys.dtype != torch.int64 or payload.dtype != torch.int64 or keys.numel() != payload.numel():
+            raise ValueError("build keys and payload must be int64 of one length")
+        self.keys, self.payload = keys, payload
+        self.ws = _ws(L.rel_join_ws_bytes(keys.numel()), keys.device)
+        self.t = JoinTableC()
+        _check(L.rel_join_build(keys.data_ptr(), payload.data_ptr(), keys.numel(),
+                                self.ws.data_ptr(), self.ws.numel(), ctypes.byref(self.t),
+                                _stream(stream)))
+
+    def count(self, probe: torch.Tensor, stream=None) -> int:
+        L = load()
+        pd = JoinProbeDesc(ctypes.pointer(self.t), probe.data_ptr(), probe.numel())
+        plan = Plan()
+        _check(L.rel_plan_size(OP_JOIN_PROBE, ctypes.byref(pd), 0, 0, None, 0,
+                               ctypes.byref(plan), _stream(stream)))
+        return int(plan.est_groups)
+
+    def probe(self, probe: torch.Tensor, capacity: int | None = None, stream=None):
+        """Returns (probe_idx int32, build_idx int32, payload int64), unspecified order."""
+        L = load()
+        if probe.dtype != torch.int64:
+            raise ValueError("probe keys must be int64")
+        if capacity is None:
+            capacity = max(1, probe.numel())
+        dev = probe.device
+        while True:
+            pi = torch.empty(capacity, dtype=torch.int32, device=dev)
+            bi = torch.empty(capacity, dtype=torch.int32, device=dev)
+            pay = torch.empty(capacity, dtype=torch.int64, device=dev)
+            n = ctypes.c_int64(0)
+            r = L.rel_join_probe(ctypes.byref(self.t), probe.data_ptr(), probe.numel(),
+                                 pi.data_ptr(), bi.data_ptr(), pay.data_ptr(), capacity,
+                                 ctypes.byref(n), _stream(stream))
+            if r == REL_E_CAPACITY and n.value > capacity:
+                capacity = n.value
+                continue
+            _check(r)
+            return pi[:n.value], bi[:n.value], pay[:n.value]

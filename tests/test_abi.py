@@ -1,0 +1,142 @@
+"""The C-ABI library: it loads, it exports exactly what include/rel.h declares,
+and host-side validation and sizing work without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2608_13696_gb300 import build as B
+from paper_2608_13696_gb300 import rel
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "rel.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rel_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return rel.load()
+
+
+def test_header_matches_binding_list():
+    assert declared_functions() == sorted(rel.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+
+
+def test_version_and_counters(L):
+    assert L.rel_version() == 100
+    assert L.rel_launch_count() == 0  # nothing launched in this process
+    assert L.rel_last_error() is not None
+
+
+def test_ws_sizes(L):
+    assert L.rel_groupby_ws_bytes(16, 4) == 256 + 16 * 8 * 5
+    assert L.rel_groupby_ws_bytes(1 << 20, 2) == 256 + (1 << 20) * 24
+    # join: next_pow2(2n) slots x (8 B key + 16 B value) + n x 16 B side list
+    assert L.rel_join_ws_bytes(1_000_000) == 256 + (1 << 21) * 24 + 1_000_000 * 16
+    assert L.rel_join_ws_bytes(0) == 256 + 16 * 24 + 16
+
+
+def _desc(n_rows=100, **over):
+    cols = (rel.Col * 2)(rel.Col(0x1000, rel.I64, 0), rel.Col(0x2000, rel.I64, 0))
+    keys = (ctypes.c_int32 * 1)(0)
+    aggs = (rel.Agg * 1)(rel.Agg(rel.OPS["sum"], 1, 0, 0))
+    preds = (rel.RangePred * 1)()
+    d = rel.GroupByDesc(n_rows, 2, 1, 0, 1, cols, keys, preds, aggs)
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d, (cols, keys, aggs, preds)
+
+
+def test_plan_from_hint_is_host_only(L):
+    d, keep = _desc()
+    plan = rel.Plan()
+    assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 1000, None, 0,
+                           ctypes.byref(plan), None) == rel.REL_OK
+    assert plan.est_groups == 1000 and plan.slots == 2048
+    assert plan.variant == rel.VAR_SMEM and plan.smem_slots == 2048
+    assert plan.workspace_bytes == L.rel_groupby_ws_bytes(2048, 1)
+    assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 5, None, 0,
+                           ctypes.byref(plan), None) == rel.REL_OK
+    assert plan.smem_slots == 8  # thread-private accumulators
+    assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 10**7, None, 0,
+                           ctypes.byref(plan), None) == rel.REL_OK
+    assert plan.variant == rel.VAR_GLOBAL and plan.slots == 1 << 25
+
+
+def test_exact_plan_reports_scratch_without_gpu(L):
+    d, keep = _desc(n_rows=1000)
+    plan = rel.Plan()
+    r = L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), rel.PLAN_EXACT, 0, None, 0,
+                        ctypes.byref(plan), None)
+    assert r == rel.REL_E_CAPACITY
+    assert plan.scratch_bytes == 256 + 2048 * 8
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_rows", -1), ("n_cols", 0), ("n_cols", 9), ("n_keys", 0), ("n_keys", 5),
+    ("n_aggs", 0), ("n_aggs", 9), ("n_preds", 5),
+])
+def test_invalid_descriptors_rejected_before_cuda(L, field, value):
+    d, keep = _desc(**{field: value})
+    plan = rel.Plan()
+    assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 10, None, 0,
+                           ctypes.byref(plan), None) == rel.REL_E_INVALID
+    assert L.rel_last_error()
+
+
+def test_bad_agg_and_packed_key_rejected(L):
+    d, keep = _desc()
+    keep[2][0].op = 7
+    plan = rel.Plan()
+    assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 10, None, 0,
+                           ctypes.byref(plan), None) == rel.REL_E_INVALID
+    # two int64 key columns cannot be packed into one 64-bit key
+    d, keep = _desc()
+    keys = (ctypes.c_int32 * 2)(0, 1)
+    d.keys_ref = keys
+    d.key_cols = keys
+    d.n_keys = 2
+    assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 10, None, 0,
+                           ctypes.byref(plan), None) == rel.REL_E_INVALID
+
+
+def test_groupby_agg_argument_checks(L):
+    d, keep = _desc()
+    plan = rel.Plan()
+    plan.slots = 24  # not a power of two
+    n = ctypes.c_int64()
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
+                             ctypes.byref(n), None) == rel.REL_E_INVALID
+    plan.slots = 1024
+    plan.smem_slots = 24
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
+                             ctypes.byref(n), None) == rel.REL_E_INVALID
+    plan.smem_slots = 0
+    # workspace too small: capacity error before any device work
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 100, 0x10, None, 0,
+                             ctypes.byref(n), None) == rel.REL_E_CAPACITY
+
+
+def test_join_argument_checks(L):
+    t = rel.JoinTableC()
+    assert L.rel_join_build(None, None, -1, None, 0, ctypes.byref(t), None) == rel.REL_E_UNSUPPORTED
+    assert L.rel_join_build(None, None, 1 << 31, None, 0, ctypes.byref(t), None) == rel.REL_E_UNSUPPORTED
+    assert L.rel_join_build(None, None, 10, None, 0, ctypes.byref(t), None) == rel.REL_E_INVALID
+    assert L.rel_join_build(0x10, 0x10, 10, 0x10, 10, ctypes.byref(t), None) == rel.REL_E_CAPACITY
+    n = ctypes.c_int64()
+    # an unbuilt handle is rejected
+    assert L.rel_join_probe(ctypes.byref(t), 0x10, 10, 0x10, 0x10, 0x10, 10, ctypes.byref(n),
+                            None) == rel.REL_E_INVALID
