@@ -46,15 +46,19 @@ def full_sizes(small: bool):
 
 # ----------------------------------------------------------------- inputs
 
-def make_inputs(sz, seed):
+def make_inputs(sz, seed, prefix=None):
+    """Seeded inputs; with prefix = {part: fraction} only those leading rows
+    (identical to the full columns' prefixes: the generator is counter-based)."""
     import oracle  # query description helpers only; no oracle computation here
     import synth
 
-    li = synth.lineitem(sz["li"], seed=seed)
+    f = prefix or {}
+    n = lambda key, part: max(1, int(sz[key] * f.get(part, 1.0)))
+    li = synth.lineitem(n("li", "lineitem"), seed=seed)
     bk, bp = synth.join_build(sz["nb"], seed=seed)
-    pk, _ = synth.join_probe(sz["np"], sz["nb"], seed=seed)
-    zk, zv = synth.zipf_kv(sz["big"], seed=seed)
-    fk, fv = synth.few_keys_kv(sz["big"], n_keys=4, seed=seed)
+    pk, _ = synth.join_probe(n("np", "join"), sz["nb"], seed=seed)
+    zk, zv = synth.zipf_kv(n("big", "zipf"), seed=seed)
+    fk, fv = synth.few_keys_kv(n("big", "fourkeys"), n_keys=4, seed=seed)
     return {"li": oracle.lineitem_query(li), "bk": bk, "bp": bp, "pk": pk,
             "zipf": oracle.kv_query(zk, zv), "four": oracle.kv_query(fk, fv)}
 
@@ -246,7 +250,7 @@ def run_reference(args, sz):
         return 0
     import oracle
     oracle.build()
-    inp = make_inputs(sz, seed=0)
+    inp = make_inputs(sz, seed=0, prefix=REF_FRACS)
     rows_full = part_rows(sz)
     for _ in range(args.warmup):
         time_oracle_parts(inp, sz, REF_FRACS)
