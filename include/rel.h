@@ -167,6 +167,33 @@ rel_status rel_groupby_agg(const rel_groupby_desc* desc, const rel_plan* plan, v
  * aggregates. */
 uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs);
 
+/* Group-by without any device allocation, for callers that cannot allocate
+ * device memory: an engine whose own pool owns all of the GPU's memory and
+ * forbids other allocations, a plugin whose host process caps device memory,
+ * or a latency-critical path that must not call cudaMalloc / cudaFree (they
+ * can synchronise the device).  The paper has no counterpart; this is an
+ * interface convenience.
+ *
+ * Same result as rel_groupby_agg, but the hash table lives in a scratch array
+ * compiled into the library (about 4.5 MiB of device memory that every GPU
+ * which loads the library keeps until the process exits), sized for
+ * max_groups <= REL_STATIC_MAX_GROUPS.  The caller passes the inputs (desc)
+ * and the outputs as for rel_groupby_agg, plus max_groups, an upper bound on
+ * the number of groups.  max_groups outside 1..REL_STATIC_MAX_GROUPS is
+ * rejected with REL_E_UNSUPPORTED before any device work; more groups than
+ * the table sized from max_groups can hold gives REL_E_OVERFLOW.
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array:
+ * each call clears what it uses before its kernels run, so sequential calls
+ * are independent, but calls that overlap on the GPU (different streams or
+ * threads without ordering between them) race and give wrong results. */
+#define REL_STATIC_MAX_GROUPS 32768
+rel_status rel_groupby_agg_static(const rel_groupby_desc* desc, int64_t max_groups,
+                                  int64_t* out_keys, int64_t* const* out_aggs,
+                                  int64_t out_capacity, int64_t* n_groups_host, void* stream);
+
 /* ----------------------------------------------------------------- join */
 
 /* Handle to a built join table.  It lives in caller memory, points into the

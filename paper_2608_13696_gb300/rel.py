@@ -92,7 +92,9 @@ _lib = None
 # every function include/rel.h declares (the ABI test checks the header agrees)
 EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join_ws_bytes",
            "rel_join_build", "rel_join_probe", "rel_last_error", "rel_launch_count",
-           "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name"]
+           "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name",
+           "rel_groupby_agg_static"]
+STATIC_MAX_GROUPS = 32768
 
 
 def lib_path() -> str:
@@ -139,6 +141,10 @@ def load(build_if_stale: bool = True):
         L.rel_profile_stop.argtypes = [vp, vp, i64]
         L.rel_kernel_name.restype = ctypes.c_char_p
         L.rel_kernel_name.argtypes = [i32]
+        L.rel_groupby_agg_static.restype = i32
+        L.rel_groupby_agg_static.argtypes = [ctypes.POINTER(GroupByDesc), i64, vp,
+                                             ctypes.POINTER(ctypes.c_void_p), i64,
+                                             ctypes.POINTER(i64), vp]
         _lib = L
         return L
 
@@ -251,6 +257,26 @@ def groupby(q: dict, plan: Plan | None = None, flags: int = 0, groups_hint: int 
         _check(r)
         g = n.value
         return keys[:g], [a[:g] for a in aggs]
+
+
+def groupby_static(q: dict, max_groups: int, capacity: int | None = None, stream=None):
+    """Group-by through rel_groupby_agg_static: the library allocates nothing
+    (its hash table is a scratch array built into librel.so), for callers
+    that cannot allocate device memory.  The outputs here are allocated by
+    the caller (this function), as the C entry point requires.  Returns
+    (keys int64[G], [agg int64[G], ...]) in unspecified group order."""
+    L = load()
+    d = _Desc(q)
+    dev = q["cols"][0].device
+    cap = max(1, capacity if capacity is not None else max_groups)
+    keys = torch.empty(cap, dtype=torch.int64, device=dev)
+    aggs = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in range(d.n_aggs)]
+    ptrs = (ctypes.c_void_p * max(1, d.n_aggs))(*[a.data_ptr() for a in aggs])
+    n = ctypes.c_int64(0)
+    _check(L.rel_groupby_agg_static(ctypes.byref(d.d), max_groups, keys.data_ptr(), ptrs, cap,
+                                    ctypes.byref(n), _stream(stream)))
+    g = n.value
+    return keys[:g], [a[:g] for a in aggs]
 
 
 class JoinTable:
