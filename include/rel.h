@@ -116,17 +116,20 @@ typedef struct {
 #define REL_PLAN_LEARNED 2u /* reserved: sample sketch + learned size / variant      */
 #define REL_PLAN_GENERIC 4u /* force the descriptor-interpreting kernel              */
 
+/* A plan fixes the table sizes; rows fall through thread-private slots, then
+ * a CTA-shared table, then the global table (each of the first two optional),
+ * so the result never depends on the plan -- only the speed does. */
 typedef struct {
-  int64_t slots;            /* global hash-table slots (power of two)           */
-  int32_t variant;          /* REL_VAR_*                                        */
-  int32_t smem_slots;       /* per-CTA table slots: 0 none, 8 thread-private,
-                               16..4096 CTA-shared                              */
+  int64_t slots;            /* global hash-table slots (power of two >= 16)     */
+  int32_t variant;          /* REL_VAR_* label of the choice                    */
+  int32_t smem_slots;       /* CTA-shared table slots: 0 or a power of two in
+                               [16, 4096]                                       */
   uint64_t workspace_bytes; /* bytes rel_groupby_agg needs in ws               */
   uint64_t scratch_bytes;   /* bytes rel_plan_size itself needs in ws          */
   int64_t est_groups;       /* estimated (or, with REL_PLAN_EXACT, exact)
                                number of groups                                 */
   uint32_t flags;           /* REL_PLAN_* used                                  */
-  int32_t reserved;
+  int32_t tiny_slots;       /* thread-private slots per CTA: 0, 8, 16 or 32     */
 } rel_plan;
 
 #define REL_OP_GROUPBY 0
@@ -146,8 +149,8 @@ typedef struct {
 rel_status rel_plan_size(int32_t op, const void* desc, uint32_t flags, int64_t groups_hint,
                          void* ws, size_t ws_bytes, rel_plan* plan, void* stream);
 
-/* Run the group-by with a plan from rel_plan_size (plan->variant may be
- * overridden by the caller; slots must be a power of two >= 16).
+/* Run the group-by with a plan from rel_plan_size (the caller may change
+ * tiny_slots / smem_slots / slots within their stated ranges).
  *  ws       : >= plan->workspace_bytes device bytes, any content on entry;
  *             the call zeroes what it uses.  Must not be shared by calls that
  *             overlap on the GPU.

@@ -6,6 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "groupby.cuh"
@@ -154,25 +157,61 @@ rel_status validate_desc(const rel_groupby_desc* d) {
   return REL_OK;
 }
 
-// Which specialised kernel (if any) computes this descriptor.
-int match_shape(const rel_groupby_desc* d, GbParams& p) {
+struct HostHeader {
+  unsigned long long n_out, n_side;
+  unsigned int overflow, timeout;
+  unsigned long long aux;
+};
+
+rel_status read_header(const void* ws, HostHeader* h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h, ws, sizeof(HostHeader), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "reading the status header");
+}
+
+// A descriptor mapped onto a kernel shape.  perm[a] is the user aggregate
+// that kernel word a computes (the KV shapes hold their words in a fixed
+// internal order).
+struct Mapped {
+  int shape = SHAPE_GENERIC;
+  int perm[REL_MAX_AGGS];
+};
+
+Mapped match_shape(const rel_groupby_desc* d, GbParams& p) {
+  Mapped m;
+  for (int a = 0; a < REL_MAX_AGGS; ++a) m.perm[a] = a;
   auto T = [&](int c) { return d->cols[c].type; };
   // key column + one int64 value column, no filter, no factors
   if (d->n_keys == 1 && d->n_preds == 0 && d->n_aggs <= 4 &&
       (T(d->key_cols[0]) == REL_I64 || T(d->key_cols[0]) == REL_I32)) {
     int vcol = -1;
     bool ok = true;
+    int at[4] = {-1, -1, -1, -1};  // user index of SUM, COUNT, MIN, MAX
+    bool dup = false;
     for (int a = 0; a < d->n_aggs && ok; ++a) {
       const rel_agg& g = d->aggs[a];
+      const int slot = g.op == REL_SUM ? 0 : g.op == REL_COUNT ? 1 : g.op == REL_MIN ? 2 : 3;
+      if (at[slot] >= 0) dup = true;
+      at[slot] = a;
       if (g.op == REL_COUNT) continue;
       if (g.nf != 0 || T(g.base_col) != REL_I64) ok = false;
       else if (vcol < 0) vcol = g.base_col;
       else if (vcol != g.base_col) ok = false;
     }
-    if (ok) {
-      p.r_a = vcol < 0 ? d->key_cols[0] : vcol;
-      if (vcol < 0 && T(p.r_a) != REL_I64) return SHAPE_GENERIC;
-      return T(d->key_cols[0]) == REL_I64 ? SHAPE_KV64 : SHAPE_KV32;
+    if (ok && vcol >= 0) {
+      p.r_a = vcol;
+      const bool k64 = T(d->key_cols[0]) == REL_I64;
+      if (!dup && d->n_aggs == 4) {
+        for (int i = 0; i < 4; ++i) m.perm[i] = at[i];
+        m.shape = k64 ? SHAPE_KV4_64 : SHAPE_KV4_32;
+      } else if (!dup && d->n_aggs == 2 && at[0] >= 0 && at[1] >= 0) {
+        m.perm[0] = at[0];
+        m.perm[1] = at[1];
+        m.shape = k64 ? SHAPE_KV2_64 : SHAPE_KV2_32;
+      } else {
+        m.shape = k64 ? SHAPE_KVRT64 : SHAPE_KVRT32;
+      }
+      return m;
     }
   }
   // (u8, u8) key, one int32 range filter, five aggregates of the form
@@ -181,13 +220,13 @@ int match_shape(const rel_groupby_desc* d, GbParams& p) {
       d->n_preds == 1 && T(d->preds[0].col) == REL_I32 && d->n_aggs == 5) {
     const rel_agg* g = d->aggs;
     auto i64 = [&](int c) { return T(c) == REL_I64; };
-    bool ok = g[0].op == REL_SUM && g[0].nf == 0 && i64(g[0].base_col) &&
-              g[1].op == REL_SUM && g[1].nf == 0 && i64(g[1].base_col) &&
-              g[2].op == REL_SUM && g[2].nf == 1 && g[2].base_col == g[1].base_col &&
-              i64(g[2].fcol[0]) && g[3].op == REL_SUM && g[3].nf == 2 &&
-              g[3].base_col == g[1].base_col && g[3].fcol[0] == g[2].fcol[0] &&
-              g[3].c[0] == g[2].c[0] && g[3].s[0] == g[2].s[0] && i64(g[3].fcol[1]) &&
-              g[4].op == REL_COUNT;
+    const bool ok = g[0].op == REL_SUM && g[0].nf == 0 && i64(g[0].base_col) &&
+                    g[1].op == REL_SUM && g[1].nf == 0 && i64(g[1].base_col) &&
+                    g[2].op == REL_SUM && g[2].nf == 1 && g[2].base_col == g[1].base_col &&
+                    i64(g[2].fcol[0]) && g[3].op == REL_SUM && g[3].nf == 2 &&
+                    g[3].base_col == g[1].base_col && g[3].fcol[0] == g[2].fcol[0] &&
+                    g[3].c[0] == g[2].c[0] && g[3].s[0] == g[2].s[0] && i64(g[3].fcol[1]) &&
+                    g[4].op == REL_COUNT;
     if (ok) {
       p.r_k0 = d->key_cols[0];
       p.r_k1 = d->key_cols[1];
@@ -196,13 +235,14 @@ int match_shape(const rel_groupby_desc* d, GbParams& p) {
       p.r_b = g[1].base_col;
       p.r_d = g[2].fcol[0];
       p.r_t = g[3].fcol[1];
-      return SHAPE_Q1;
+      m.shape = SHAPE_Q1;
     }
   }
-  return SHAPE_GENERIC;
+  return m;
 }
 
-void fill_params(const rel_groupby_desc* d, GbParams& p) {
+// Kernel parameters of a descriptor, aggregates in the mapped order.
+void fill_params(const rel_groupby_desc* d, const int* perm, GbParams& p) {
   std::memset(&p, 0, sizeof p);
   p.n_rows = d->n_rows;
   p.n_cols = d->n_cols;
@@ -228,7 +268,7 @@ void fill_params(const rel_groupby_desc* d, GbParams& p) {
     p.pred_hi[i] = d->preds[i].hi;
   }
   for (int a = 0; a < d->n_aggs; ++a) {
-    const rel_agg& g = d->aggs[a];
+    const rel_agg& g = d->aggs[perm[a]];
     p.aop[a] = g.op;
     p.abase[a] = g.op == REL_COUNT ? 0 : g.base_col;
     p.anf[a] = g.op == REL_COUNT ? 0 : g.nf;
@@ -241,21 +281,9 @@ void fill_params(const rel_groupby_desc* d, GbParams& p) {
   }
 }
 
-// Rows per tile so that the staging ring fits next to the backend's table.
-int choose_tile(const GbParams& p, uint64_t be_bytes, int mode) {
-  uint64_t row_bytes = 0;
-  for (int c = 0; c < p.n_cols; ++c) row_bytes += (uint64_t)p.csize[c];
-  const uint64_t budget = SMEM_LIMIT - 256 - ((be_bytes + 127) & ~127ull);
-  const uint64_t target = mode == MODE_GLOBAL || mode == MODE_KEYSET ? 16384 : 65536;
-  int t = 4096;
-  while (t > 256 && ((uint64_t)t * row_bytes > target || (uint64_t)GB_STAGES * t * row_bytes > budget))
-    t >>= 1;
-  if ((uint64_t)GB_STAGES * t * row_bytes > budget) return 0;
-  return t;
-}
-
-void set_stages(GbParams& p, int tile) {
+void set_stages(GbParams& p, int tile, int stages) {
   p.tile_rows = tile;
+  p.n_stages = stages;
   uint32_t off = 0;
   for (int c = 0; c < p.n_cols; ++c) {
     p.stage_off[c] = off;
@@ -270,36 +298,82 @@ bool tma_ok(const GbParams& p) {
   return true;
 }
 
-struct HostHeader {
-  unsigned long long n_out, n_side;
-  unsigned int overflow, timeout;
-  unsigned long long aux;
+// Occupancy of each configuration, cached (the occupancy query is not free).
+struct OccKey {
+  int shape, mode, tma;
+  uint32_t tiny, shared, tile, stages, stage_bytes;
+  bool operator<(const OccKey& o) const {
+    return std::tie(shape, mode, tma, tiny, shared, tile, stages, stage_bytes) <
+           std::tie(o.shape, o.mode, o.tma, o.tiny, o.shared, o.tile, o.stages, o.stage_bytes);
+  }
 };
+std::mutex g_occ_mu;
+std::map<OccKey, int> g_occ[64];
 
-rel_status read_header(const void* ws, HostHeader* h, cudaStream_t st) {
-  cudaError_t e = cudaMemcpyAsync(h, ws, sizeof(HostHeader), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "reading the status header");
+int cached_occupancy(GbParams& p, int shape, int mode, bool tma) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  dev &= 63;
+  const OccKey k{shape, mode, tma, p.tiny_slots, p.smem_slots, (uint32_t)p.tile_rows,
+                 (uint32_t)p.n_stages, p.stage_bytes};
+  {
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    auto it = g_occ[dev].find(k);
+    if (it != g_occ[dev].end()) return it->second;
+  }
+  const int occ = gb_ctas_per_sm(p, shape, mode, tma);
+  std::lock_guard<std::mutex> lock(g_occ_mu);
+  g_occ[dev][k] = occ;
+  return occ;
 }
 
-// Launch the fused kernel for one mode, degrading to smaller per-CTA tables
-// when the requested one does not fit in shared memory.
-rel_status run_main(GbParams& p, int shape, int mode, bool generic_only, cudaStream_t st) {
-  if (generic_only) shape = SHAPE_GENERIC;
-  for (;;) {
-    const uint64_t be = gb_backend_smem_bytes(mode, shape, p.smem_slots);
-    const int tile = choose_tile(p, be, mode);
-    if (tile > 0) {
-      set_stages(p, tile);
-      return gb_launch_main(p, shape, mode, tma_ok(p), st);
+// Pick rows per tile and ring depth: enough bytes in flight per SM to cover
+// HBM latency (>= 64 KB), then as many resident warps as possible.
+bool configure_stages(GbParams& p, int shape, int mode, bool tma) {
+  if (!tma) {
+    set_stages(p, 1024, 2);
+    return cached_occupancy(p, shape, mode, false) > 0;
+  }
+  uint64_t row_bytes = 0;
+  for (int c = 0; c < p.n_cols; ++c) row_bytes += (uint64_t)p.csize[c];
+  int best_t = 0, best_s = 0;
+  long best_score = -1;
+  for (int t : {2048, 1024, 512, 256}) {
+    for (int ns : {4, 3, 2}) {
+      if ((uint64_t)t * row_bytes > 48 * 1024) continue;
+      set_stages(p, t, ns);
+      const int occ = cached_occupancy(p, shape, mode, true);
+      if (occ < 1) continue;
+      const uint64_t inflight = (uint64_t)occ * ns * p.stage_bytes;
+      const int warps = occ * (GB_BLOCK / 32);
+      const long score = (inflight >= 64 * 1024 ? 1000000L : 0L) +
+                         (long)(warps > 32 ? 32 : warps) * 1000 + (long)(t / 256) * 10 + ns;
+      if (score > best_score) {
+        best_score = score;
+        best_t = t;
+        best_s = ns;
+      }
     }
-    if (mode == MODE_TINY) {
-      mode = MODE_SHARED;
-      p.smem_slots = 256;
-    } else if ((mode == MODE_SHARED || mode == MODE_KEYSET) && p.smem_slots > 16) {
+  }
+  if (best_score < 0) return false;
+  set_stages(p, best_t, best_s);
+  return true;
+}
+
+// Launch the fused kernel, shrinking the per-CTA tables when they do not fit.
+rel_status run_main(GbParams& p, int shape, int mode, cudaStream_t st) {
+  const bool tma = tma_ok(p);
+  for (;;) {
+    if (configure_stages(p, shape, mode, tma)) return gb_launch_main(p, shape, mode, tma, st);
+    if (p.tiny_slots > 8) {
+      p.tiny_slots >>= 1;
+      p.tiny_probes = p.tiny_probes > p.tiny_slots ? p.tiny_slots : p.tiny_probes;
+    } else if (p.tiny_slots) {
+      p.tiny_slots = 0;
+      p.tiny_probes = 0;
+    } else if (p.smem_slots > 16) {
       p.smem_slots >>= 1;
-    } else if (mode == MODE_SHARED) {
-      mode = MODE_GLOBAL;
+    } else if (p.smem_slots && mode != MODE_KEYSET) {
       p.smem_slots = 0;
     } else {
       set_error("group-by: rows too wide to stage");
@@ -312,18 +386,38 @@ uint64_t gb_ws_bytes(int64_t slots, int32_t n_aggs) {
   return HEADER_BYTES + (uint64_t)slots * 8ull * (1ull + (uint64_t)n_aggs);
 }
 
-void choose_variant(int64_t est, int n_aggs, rel_plan* plan) {
-  if (est <= 6 && n_aggs <= 6) {
+// Per-CTA layers for an expected number of groups.
+void choose_layers(int64_t est, int words, rel_plan* plan) {
+  plan->tiny_slots = 0;
+  plan->smem_slots = 0;
+  if (est <= 6 && words <= 6) {
     plan->variant = REL_VAR_SMEM;
-    plan->smem_slots = TINY_SLOTS;
+    plan->tiny_slots = 8;
+  } else if (est <= 12 && words <= 4) {
+    plan->variant = REL_VAR_SMEM;
+    plan->tiny_slots = 16;
+  } else if (est <= 24 && words <= 2) {
+    plan->variant = REL_VAR_SMEM;
+    plan->tiny_slots = 32;
   } else if (est <= 2048) {
     plan->variant = REL_VAR_SMEM;
-    plan->smem_slots = (int32_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
-    if (plan->smem_slots > 4096) plan->smem_slots = 4096;
+    plan->tiny_slots = words <= 6 ? 8 : 0;  // catches a skewed input's hottest keys
+    plan->smem_slots = (int32_t)next_pow2((uint64_t)(2 * est));
   } else {
     plan->variant = REL_VAR_GLOBAL;
-    plan->smem_slots = 0;
+    plan->tiny_slots = words <= 6 ? 8 : 0;
+    plan->smem_slots = 2048;
   }
+}
+
+// Probe limits of the per-CTA layers: a layer that must hold every group
+// scans it all; a cache in front of a larger layer gives up early.
+void set_layers(GbParams& p, const rel_plan* plan) {
+  p.tiny_slots = (uint32_t)plan->tiny_slots;
+  p.smem_slots = (uint32_t)plan->smem_slots;
+  const bool tiny_only = p.tiny_slots && !p.smem_slots && plan->variant == REL_VAR_SMEM;
+  p.tiny_probes = tiny_only ? p.tiny_slots : (p.tiny_slots ? 2u : 0u);
+  p.shared_probes = plan->variant == REL_VAR_SMEM ? 16u : 4u;
 }
 
 rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint, void* ws,
@@ -332,6 +426,9 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
   if (r) return r;
   std::memset(plan, 0, sizeof *plan);
   plan->flags = flags;
+  GbParams p;
+  Mapped m = match_shape(d, p);
+  if (flags & REL_PLAN_GENERIC) m.shape = SHAPE_GENERIC;
   int64_t est;
   if (hint > 0) {
     est = hint;
@@ -346,17 +443,55 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
     if (d->n_rows == 0) {
       est = 0;
     } else {
-      GbParams p;
-      fill_params(d, p);
-      const int shape = match_shape(d, p);
-      p.hdr = (WsHeader*)ws;
-      p.tkeys = (uint64_t*)((uint8_t*)ws + HEADER_BYTES);
-      p.log2_slots = log2_pow2(set_slots);
-      p.max_probe = (uint32_t)(set_slots < 4096 ? set_slots : 4096);
-      p.smem_slots = 1024;
+      // reduced descriptor: the key and filter columns, one COUNT
+      rel_col cols[REL_MAX_COLS];
+      int32_t keys[REL_MAX_KEYS];
+      rel_range_pred preds[REL_MAX_PREDS];
+      int map[REL_MAX_COLS];
+      for (int c = 0; c < REL_MAX_COLS; ++c) map[c] = -1;
+      int nc = 0;
+      auto use = [&](int c) {
+        if (map[c] < 0) {
+          map[c] = nc;
+          cols[nc++] = d->cols[c];
+        }
+        return map[c];
+      };
+      for (int k = 0; k < d->n_keys; ++k) keys[k] = use(d->key_cols[k]);
+      for (int i = 0; i < d->n_preds; ++i) {
+        preds[i] = d->preds[i];
+        preds[i].col = use(d->preds[i].col);
+      }
+      rel_agg cnt;
+      std::memset(&cnt, 0, sizeof cnt);
+      cnt.op = REL_COUNT;
+      rel_groupby_desc kd = *d;
+      kd.n_cols = nc;
+      kd.cols = cols;
+      kd.key_cols = keys;
+      kd.preds = preds;
+      kd.n_aggs = 1;
+      kd.aggs = &cnt;
+      GbParams kp;
+      const int ident[REL_MAX_AGGS] = {0, 1, 2, 3, 4, 5, 6, 7};
+      fill_params(&kd, ident, kp);
+      // one int64 key and no filter: the specialised key/value reader, with
+      // the key column standing in as the (unused) value column
+      int kshape = SHAPE_GENERIC;
+      if (m.shape != SHAPE_GENERIC && kd.n_keys == 1 && kd.n_preds == 0 &&
+          kd.cols[keys[0]].type == REL_I64) {
+        kshape = SHAPE_KVRT64;
+        kp.r_a = keys[0];
+      }
+      kp.hdr = (WsHeader*)ws;
+      kp.tkeys = (uint64_t*)((uint8_t*)ws + HEADER_BYTES);
+      kp.log2_slots = log2_pow2(set_slots);
+      kp.max_probe = (uint32_t)(set_slots < 4096 ? set_slots : 4096);
+      kp.smem_slots = 2048;
+      kp.shared_probes = 4;
       cudaError_t e = cudaMemsetAsync(ws, 0, plan->scratch_bytes, st);
       if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
-      r = run_main(p, shape, MODE_KEYSET, (flags & REL_PLAN_GENERIC) != 0, st);
+      r = run_main(kp, kshape, MODE_KEYSET, st);
       if (r) return r;
       HostHeader h;
       if ((r = read_header(ws, &h, st))) return r;
@@ -369,7 +504,7 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
   }
   plan->est_groups = est;
   plan->slots = (int64_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
-  choose_variant(est, d->n_aggs, plan);
+  choose_layers(est, gb_shape_width(m.shape), plan);
   plan->workspace_bytes = gb_ws_bytes(plan->slots, d->n_aggs);
   return REL_OK;
 }
@@ -460,9 +595,8 @@ int64_t rel_profile_stop(int32_t* ids, float* ms, int64_t max) {
 }
 
 const char* rel_kernel_name(int32_t id) {
-  static const char* names[] = {"gb_main_global", "gb_main_tiny", "gb_main_shared",
-                                "gb_main_keyset", "gb_compact", "join_build",
-                                "join_probe", "join_count"};
+  static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
+                                "join_build", "join_probe", "join_count"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 
@@ -503,10 +637,12 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   if (!plan) return set_error("group-by: NULL plan"), REL_E_INVALID;
   if (plan->slots < 16 || !is_pow2((uint64_t)plan->slots))
     return set_error("group-by: plan slots must be a power of two >= 16"), REL_E_INVALID;
-  const int32_t ss = plan->smem_slots;
-  if (!(ss == 0 || ss == TINY_SLOTS || (ss >= 16 && ss <= 4096 && is_pow2((uint64_t)ss))))
-    return set_error("group-by: smem_slots must be 0, 8 or a power of two in [16, 4096]"),
+  const int32_t ss = plan->smem_slots, ts = plan->tiny_slots;
+  if (!(ss == 0 || (ss >= 16 && ss <= SHARED_MAX_SLOTS && is_pow2((uint64_t)ss))))
+    return set_error("group-by: smem_slots must be 0 or a power of two in [16, 4096]"),
            REL_E_INVALID;
+  if (!(ts == 0 || ts == 8 || ts == 16 || ts == 32))
+    return set_error("group-by: tiny_slots must be 0, 8, 16 or 32"), REL_E_INVALID;
   const uint64_t need = gb_ws_bytes(plan->slots, d->n_aggs);
   if (!ws || ws_bytes < need) {
     set_error("group-by: workspace needs %llu bytes", (unsigned long long)need);
@@ -514,28 +650,39 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   }
   if (out_capacity < 0 || (out_capacity > 0 && (!out_keys || !out_aggs)))
     return set_error("group-by: bad outputs"), REL_E_INVALID;
+  for (int a = 0; a < d->n_aggs; ++a)
+    if (out_capacity > 0 && !out_aggs[a])
+      return set_error("group-by: NULL aggregate output"), REL_E_INVALID;
+  GbParams p;
+  Mapped m = match_shape(d, p);
+  if (plan->flags & REL_PLAN_GENERIC) {
+    m.shape = SHAPE_GENERIC;
+    for (int a = 0; a < REL_MAX_AGGS; ++a) m.perm[a] = a;
+  }
+  const GbParams roles = p;
+  fill_params(d, m.perm, p);
+  p.r_k0 = roles.r_k0;
+  p.r_k1 = roles.r_k1;
+  p.r_pred = roles.r_pred;
+  p.r_a = roles.r_a;
+  p.r_b = roles.r_b;
+  p.r_d = roles.r_d;
+  p.r_t = roles.r_t;
   GbOut o;
   std::memset(&o, 0, sizeof o);
   o.keys = out_keys;
   o.capacity = out_capacity;
-  for (int a = 0; a < d->n_aggs; ++a) {
-    o.aggs[a] = out_capacity > 0 ? out_aggs[a] : nullptr;
-    if (out_capacity > 0 && !o.aggs[a]) return set_error("group-by: NULL aggregate output"), REL_E_INVALID;
-  }
+  for (int a = 0; a < d->n_aggs; ++a) o.aggs[a] = out_capacity > 0 ? out_aggs[m.perm[a]] : nullptr;
   cudaStream_t st = as_stream(stream);
-  GbParams p;
-  fill_params(d, p);
-  const int shape = match_shape(d, p);
   p.hdr = (WsHeader*)ws;
   p.tkeys = (uint64_t*)((uint8_t*)ws + HEADER_BYTES);
   p.taggs = (unsigned long long*)(p.tkeys + plan->slots);
   p.log2_slots = log2_pow2((uint64_t)plan->slots);
   p.max_probe = (uint32_t)(plan->slots < 4096 ? plan->slots : 4096);
-  p.smem_slots = (uint32_t)(ss >= 16 ? ss : 0);
-  const int mode = ss == TINY_SLOTS ? MODE_TINY : ss >= 16 ? MODE_SHARED : MODE_GLOBAL;
+  set_layers(p, plan);
   cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
-  if ((r = run_main(p, shape, mode, (plan->flags & REL_PLAN_GENERIC) != 0, st))) return r;
+  if ((r = run_main(p, m.shape, MODE_LAYERED, st))) return r;
   if ((r = gb_launch_compact(p, o, st))) return r;
   if (!n_groups_host) return REL_OK;
   HostHeader h;

@@ -1,25 +1,25 @@
 // Fused filter + hash group-by kernels for sm_103a.
 //
 // One persistent launch streams every column of the query through shared
-// memory with the TMA bulk-copy engine (a ring of GB_STAGES stages completed
-// on mbarriers), evaluates the range filter, the packed group key and the
+// memory with the TMA bulk-copy engine (a ring of 2-4 stages completed on
+// mbarriers), evaluates the range filter, the packed group key and the
 // product-form aggregate inputs in registers -- no expression interpreter and
 // no materialised mask, the instruction overheads the paper attributes to
 // compute_column_kernel and transform_kernel (Sec. 7) -- and folds each row
-// into a table:
-//   MODE_TINY   : up to 8 groups per CTA, each thread owning private
-//                 accumulators in shared memory (no atomics on the hot path);
-//   MODE_SHARED : a CTA-shared open-addressing table with shared-memory
-//                 atomics (the privatised aggregation of
-//                 single_pass_shmem_aggs_kernel, Sec. 7);
-//   MODE_GLOBAL : one open-addressing table in global memory;
-//   MODE_KEYSET : keys only, counting distinct keys (the exact sizing pass).
-// Per-CTA tables spill rows they cannot hold to the global table and merge
-// into it at the end, so every mode produces the same exact groups.  A
-// compaction kernel then turns occupied slots into dense output rows with a
-// warp ballot / popc and one atomic per warp.
-#include <algorithm>
-
+// into a stack of tables, first one that holds the key wins:
+//   1. thread-private: up to 32 keys per CTA, each thread owning private
+//      accumulator columns in shared memory -- no atomics, so the hottest
+//      keys of a skewed input never serialise;
+//   2. CTA-shared: an open-addressing table in shared memory updated with
+//      shared-memory atomics (the privatised aggregation of
+//      single_pass_shmem_aggs_kernel, Sec. 7);
+//   3. global: one open-addressing table in device memory (CAS claim, then
+//      fire-and-forget RED atomics).
+// Rows a per-CTA table cannot hold fall through to the next layer, and both
+// per-CTA tables merge into the global one at the end, so every layer
+// configuration yields the same exact groups.  A compaction kernel turns
+// occupied slots into dense output rows (warp ballot / popc, one atomic per
+// warp).  MODE_KEYSET counts distinct keys instead (the exact sizing pass).
 #include "groupby.cuh"
 
 namespace rel {
@@ -37,15 +37,15 @@ struct SmemView {
     }
   }
   template <class T>
-  __device__ __forceinline__ T at(const GbParams& p, int c, int r) const {
-    return ((const T*)(base + p.stage_off[c]))[r];
+  __device__ __forceinline__ const T* ptr(const GbParams& p, int c) const {
+    return (const T*)(base + p.stage_off[c]);
   }
 };
 
 struct GlobalView {
   int64_t row0;
   __device__ __forceinline__ int64_t get(const GbParams& p, int c, int r) const {
-    int64_t i = row0 + r;
+    const int64_t i = row0 + r;
     switch (p.ctype[c]) {
       case REL_U8: return (int64_t)__ldg(p.col[c] + i);
       case REL_I32: return (int64_t)__ldg((const int32_t*)p.col[c] + i);
@@ -53,29 +53,37 @@ struct GlobalView {
     }
   }
   template <class T>
-  __device__ __forceinline__ T at(const GbParams& p, int c, int r) const {
-    return (T)__ldg((const T*)p.col[c] + row0 + r);
+  __device__ __forceinline__ const T* ptr(const GbParams& p, int c) const {
+    return (const T*)p.col[c] + row0;
   }
 };
 
-template <>
-__device__ __forceinline__ int64_t GlobalView::at<int64_t>(const GbParams& p, int c, int r) const {
-  return (int64_t)__ldg((const long long*)p.col[c] + row0 + r);
-}
+template <int A>
+struct Vals {
+  uint64_t v[A];
+};
 
 // ------------------------------------------------------------- row shapes
+// prep(): per-tile column pointers (hoisted out of the row loop).
 // row(): false when the filter rejects the row; else the stored key
-// ek = key ^ KEY_FLIP and the encoded aggregate inputs x[0..n_aggs).
+// ek = key ^ KEY_FLIP and the encoded aggregate words x.v[0..A).
 
 // Any descriptor within the REL_MAX_* limits, read from the kernel params.
 struct ShapeGeneric {
-  template <int A, class V>
+  static constexpr int A = REL_MAX_AGGS;
+  static constexpr bool RT = true;  // aggregate kinds known only at run time
+  static constexpr uint32_t UMAX = 0;
+  template <class V>
+  __device__ __forceinline__ static V prep(const GbParams&, const V& v) {
+    return v;
+  }
+  template <class V>
   __device__ __forceinline__ static bool row(const GbParams& p, const V& v, int r, uint64_t& ek,
-                                             uint64_t (&x)[A]) {
+                                             Vals<A>& x) {
 #pragma unroll
     for (int i = 0; i < REL_MAX_PREDS; ++i) {
       if (i < p.n_preds) {
-        int64_t d = v.get(p, p.pred_col[i], r);
+        const int64_t d = v.get(p, p.pred_col[i], r);
         if (d < p.pred_lo[i] || d > p.pred_hi[i]) return false;
       }
     }
@@ -93,16 +101,17 @@ struct ShapeGeneric {
 #pragma unroll
     for (int a = 0; a < A; ++a) {
       if (a < p.n_aggs) {
-        int op = p.aop[a];
+        const int op = p.aop[a];
         if (op == REL_COUNT) {
-          x[a] = 1;
+          x.v[a] = 1;
         } else {
           uint64_t val = (uint64_t)v.get(p, p.abase[a], r);
 #pragma unroll
           for (int f = 0; f < 2; ++f)
             if (f < p.anf[a])
-              val *= (uint64_t)p.ac[a][f] + (uint64_t)p.as[a][f] * (uint64_t)v.get(p, p.afcol[a][f], r);
-          x[a] = agg_encode(op, (int64_t)val);
+              val *= (uint64_t)p.ac[a][f] +
+                     (uint64_t)p.as[a][f] * (uint64_t)v.get(p, p.afcol[a][f], r);
+          x.v[a] = agg_encode(op, (int64_t)val);
         }
       }
     }
@@ -110,70 +119,143 @@ struct ShapeGeneric {
   }
 };
 
-// keep lo <= pred[i] <= hi (i32 column); key = (u8 k0 << 8) | u8 k1;
+// keep lo <= pred <= hi (int32 column); key = (u8 k0 << 8) | u8 k1;
 // sum(a), sum(b), sum(b*(c0 + s0*d)), sum(b*(c0 + s0*d)*(c1 + s1*t)), count.
 struct ShapeQ1 {
-  template <int A, class V>
-  __device__ __forceinline__ static bool row(const GbParams& p, const V& v, int r, uint64_t& ek,
-                                             uint64_t (&x)[A]) {
-    static_assert(A == 5, "Q1 shape has five aggregates");
-    int64_t d = (int64_t)v.template at<int32_t>(p, p.r_pred, r);
-    if (d < p.pred_lo[0] || d > p.pred_hi[0]) return false;
-    uint64_t k0 = v.template at<uint8_t>(p, p.r_k0, r);
-    uint64_t k1 = v.template at<uint8_t>(p, p.r_k1, r);
+  static constexpr int A = 5;
+  static constexpr bool RT = false;
+  static constexpr uint32_t UMAX = 0;
+  struct Tile {
+    const int32_t* pred;
+    const uint8_t *k0, *k1;
+    const int64_t *a, *b, *d, *t;
+    int64_t lo, hi;
+    uint64_t c0, s0, c1, s1;
+  };
+  template <class V>
+  __device__ __forceinline__ static Tile prep(const GbParams& p, const V& v) {
+    return Tile{v.template ptr<int32_t>(p, p.r_pred), v.template ptr<uint8_t>(p, p.r_k0),
+                v.template ptr<uint8_t>(p, p.r_k1),   v.template ptr<int64_t>(p, p.r_a),
+                v.template ptr<int64_t>(p, p.r_b),    v.template ptr<int64_t>(p, p.r_d),
+                v.template ptr<int64_t>(p, p.r_t),    p.pred_lo[0],
+                p.pred_hi[0],                         (uint64_t)p.ac[2][0],
+                (uint64_t)p.as[2][0],                 (uint64_t)p.ac[3][1],
+                (uint64_t)p.as[3][1]};
+  }
+  __device__ __forceinline__ static bool row(const GbParams&, const Tile& q, int r, uint64_t& ek,
+                                             Vals<A>& x) {
+    const int64_t d = (int64_t)q.pred[r];
+    if (d < q.lo || d > q.hi) return false;
+    const uint64_t k0 = q.k0[r];
+    const uint64_t k1 = q.k1[r];
     ek = ((k0 << 8) | k1) ^ KEY_FLIP;
-    uint64_t qa = (uint64_t)v.template at<int64_t>(p, p.r_a, r);
-    uint64_t pb = (uint64_t)v.template at<int64_t>(p, p.r_b, r);
-    uint64_t dd = (uint64_t)v.template at<int64_t>(p, p.r_d, r);
-    uint64_t tt = (uint64_t)v.template at<int64_t>(p, p.r_t, r);
-    uint64_t f0 = (uint64_t)p.ac[2][0] + (uint64_t)p.as[2][0] * dd;
-    uint64_t f1 = (uint64_t)p.ac[3][1] + (uint64_t)p.as[3][1] * tt;
-    uint64_t dp = pb * f0;
-    x[0] = qa;
-    x[1] = pb;
-    x[2] = dp;
-    x[3] = dp * f1;
-    x[4] = 1;
+    const uint64_t qa = (uint64_t)q.a[r];
+    const uint64_t pb = (uint64_t)q.b[r];
+    const uint64_t dd = (uint64_t)q.d[r];
+    const uint64_t tt = (uint64_t)q.t[r];
+    const uint64_t f0 = q.c0 + q.s0 * dd;
+    const uint64_t f1 = q.c1 + q.s1 * tt;
+    const uint64_t dp = pb * f0;
+    x.v[0] = qa;
+    x.v[1] = pb;
+    x.v[2] = dp;
+    x.v[3] = dp * f1;
+    x.v[4] = 1;
     return true;
   }
 };
 
-// key column (int64 or int32), one int64 value column, any ops, no filter.
+// key column (int64 / int32) + one int64 value column, runtime ops, no filter.
 template <class KT>
-struct ShapeKV {
-  template <int A, class V>
-  __device__ __forceinline__ static bool row(const GbParams& p, const V& v, int r, uint64_t& ek,
-                                             uint64_t (&x)[A]) {
-    int64_t key = (int64_t)v.template at<KT>(p, p.key_col[0], r);
-    int64_t val = v.template at<int64_t>(p, p.r_a, r);
+struct ShapeKVRT {
+  static constexpr int A = 4;
+  static constexpr bool RT = true;
+  static constexpr uint32_t UMAX = 0;
+  struct Tile {
+    const KT* k;
+    const int64_t* v;
+  };
+  template <class V>
+  __device__ __forceinline__ static Tile prep(const GbParams& p, const V& v) {
+    return Tile{v.template ptr<KT>(p, p.key_col[0]), v.template ptr<int64_t>(p, p.r_a)};
+  }
+  __device__ __forceinline__ static bool row(const GbParams& p, const Tile& q, int r, uint64_t& ek,
+                                             Vals<A>& x) {
+    const int64_t key = (int64_t)q.k[r];
+    const int64_t val = q.v[r];
     ek = (uint64_t)key ^ KEY_FLIP;
 #pragma unroll
     for (int a = 0; a < A; ++a)
-      if (a < p.n_aggs) x[a] = agg_encode(p.aop[a], val);
+      if (a < p.n_aggs) x.v[a] = agg_encode(p.aop[a], val);
     return true;
   }
 };
 
+// key + int64 value; NA = 4: (sum, count, min, max), NA = 2: (sum, count).
+template <class KT, int NA>
+struct ShapeKV {
+  static constexpr int A = NA;
+  static constexpr bool RT = false;
+  static constexpr uint32_t UMAX = NA == 4 ? 0xCu : 0u;
+  struct Tile {
+    const KT* k;
+    const int64_t* v;
+  };
+  template <class V>
+  __device__ __forceinline__ static Tile prep(const GbParams& p, const V& v) {
+    return Tile{v.template ptr<KT>(p, p.key_col[0]), v.template ptr<int64_t>(p, p.r_a)};
+  }
+  __device__ __forceinline__ static bool row(const GbParams&, const Tile& q, int r, uint64_t& ek,
+                                             Vals<A>& x) {
+    const int64_t key = (int64_t)q.k[r];
+    const uint64_t val = (uint64_t)q.v[r];
+    ek = (uint64_t)key ^ KEY_FLIP;
+    x.v[0] = val;
+    x.v[1] = 1;
+    if constexpr (NA == 4) {
+      x.v[2] = val ^ MIN_FLIP;
+      x.v[3] = val ^ MAX_FLIP;
+    }
+    return true;
+  }
+};
+
+template <class S>
+__device__ __forceinline__ bool is_umax(const GbParams& p, int a) {
+  if constexpr (S::RT)
+    return (p.umax_mask >> a) & 1u;
+  else
+    return (S::UMAX >> a) & 1u;
+}
+
+template <class S>
+__device__ __forceinline__ bool live_agg(const GbParams& p, int a) {
+  if constexpr (S::RT)
+    return a < p.n_aggs;
+  else
+    return true;
+}
+
 // -------------------------------------------------------------- table ops
 
-template <int A>
-__device__ __forceinline__ void apply_global(const GbParams& p, unsigned long long* w,
-                                             const uint64_t (&x)[A]) {
+template <class S>
+__device__ __forceinline__ void red_words(const GbParams& p, unsigned long long* w,
+                                          const Vals<S::A>& x) {
 #pragma unroll
-  for (int a = 0; a < A; ++a) {
-    if (a < p.n_aggs) {
-      if ((p.umax_mask >> a) & 1u)
-        atomicMax(w + a, (unsigned long long)x[a]);
+  for (int a = 0; a < S::A; ++a) {
+    if (live_agg<S>(p, a)) {
+      if (is_umax<S>(p, a))
+        atomicMax(w + a, (unsigned long long)x.v[a]);
       else
-        atomicAdd(w + a, (unsigned long long)x[a]);
+        atomicAdd(w + a, (unsigned long long)x.v[a]);
     }
   }
 }
 
 // Insert-or-accumulate into the global table; bounded linear probing.
-template <int A>
+template <class S>
 __device__ __forceinline__ bool gtab_update_inl(const GbParams& p, uint64_t ek,
-                                                const uint64_t (&x)[A]) {
+                                                const Vals<S::A>& x) {
   const uint64_t mask = (1ull << p.log2_slots) - 1;
   uint64_t s = slot_of(ek, p.log2_slots);
   for (uint32_t i = 0; i < p.max_probe; ++i) {
@@ -183,7 +265,7 @@ __device__ __forceinline__ bool gtab_update_inl(const GbParams& p, uint64_t ek,
       if (k == 0) k = ek;
     }
     if (k == ek) {
-      apply_global<A>(p, p.taggs + s * (uint64_t)p.n_aggs, x);
+      red_words<S>(p, p.taggs + s * (uint64_t)p.n_aggs, x);
       return true;
     }
     s = (s + 1) & mask;
@@ -192,311 +274,319 @@ __device__ __forceinline__ bool gtab_update_inl(const GbParams& p, uint64_t ek,
   return false;
 }
 
-// Out-of-line copy for the cold paths (spills and end-of-kernel merges).
-template <int A>
-__device__ __noinline__ bool gtab_update(const GbParams& p, uint64_t ek, const uint64_t (&x)[A]) {
-  return gtab_update_inl<A>(p, ek, x);
+// Out-of-line copy for the colder paths (values passed in registers).
+template <class S>
+__device__ __noinline__ bool gtab_update(const GbParams& p, uint64_t ek, const Vals<S::A>& x) {
+  return gtab_update_inl<S>(p, ek, x);
 }
 
-// Key set for the exact distinct count: true when this call claimed the key.
-__device__ __noinline__ void gset_insert(const GbParams& p, uint64_t ek) {
+// Key set for the exact distinct count; false when the set overflowed.
+__device__ __noinline__ bool gset_insert(const GbParams& p, uint64_t ek) {
   const uint64_t mask = (1ull << p.log2_slots) - 1;
   uint64_t s = slot_of(ek, p.log2_slots);
   for (uint32_t i = 0; i < p.max_probe; ++i) {
     uint64_t k = ld_relaxed(p.tkeys + s);
-    if (k == ek) return;
+    if (k == ek) return true;
     if (k == 0) {
       k = atomicCAS((unsigned long long*)(p.tkeys + s), 0ull, (unsigned long long)ek);
       if (k == 0) {
         atomicAdd(&p.hdr->aux, 1ull);
-        return;
+        return true;
       }
-      if (k == ek) return;
+      if (k == ek) return true;
     }
     s = (s + 1) & mask;
   }
   atomicOr(&p.hdr->overflow, 1u);
-}
-
-template <int A>
-__device__ __forceinline__ void side_update(const GbParams& p, const uint64_t (&x)[A]) {
-  atomicAdd(&p.hdr->n_side, 1ull);
-  apply_global<A>(p, p.hdr->side_aggs, x);
+  return false;
 }
 
 // ---------------------------------------------------------------- backends
 
-template <int A>
-struct BeGlobal {
-  static constexpr int ID = relhost::K_GB_GLOBAL;
-  __host__ __device__ static uint64_t bytes(int, uint32_t) { return 0; }
-  __device__ void bind(uint8_t*, const GbParams&) {}
-  __device__ void init(const GbParams&) {}
-  __device__ __forceinline__ void update(const GbParams& p, uint64_t ek, const uint64_t (&x)[A]) {
-    gtab_update_inl<A>(p, ek, x);
-  }
-  __device__ void flush(const GbParams&) {}
-};
+constexpr uint32_t TINY_MULT = 0x9E3779B1u;
+constexpr uint32_t SHARED_MULT = 0x85EBCA77u;
 
-// Up to TINY_SLOTS keys per CTA; thread-private accumulator columns
-// acc[slot][a][thread] in shared memory, reduced and merged at the end.
-template <int A>
-struct BeTiny {
-  static constexpr int ID = relhost::K_GB_TINY;
-  uint64_t* tk;
-  uint64_t* acc;
-  uint64_t* res;
-  __host__ __device__ static uint64_t bytes(int, uint32_t) {
-    return 8ull * (TINY_SLOTS + (uint64_t)TINY_SLOTS * A * GB_BLOCK + TINY_SLOTS * A);
-  }
-  __device__ void bind(uint8_t* area, const GbParams&) {
-    tk = (uint64_t*)area;
-    acc = tk + TINY_SLOTS;
-    res = acc + (size_t)TINY_SLOTS * A * GB_BLOCK;
-  }
-  __device__ void init(const GbParams&) {
-    for (int i = threadIdx.x; i < TINY_SLOTS * (1 + A * GB_BLOCK); i += GB_BLOCK) tk[i] = 0;
-  }
-  __device__ __forceinline__ void update(const GbParams& p, uint64_t ek, const uint64_t (&x)[A]) {
-    uint32_t s = small_slot_of(ek, TINY_SLOTS - 1);
-#pragma unroll 1
-    for (int i = 0; i < TINY_SLOTS; ++i) {
-      uint64_t k = *(volatile uint64_t*)(tk + s);
-      if (k == 0) {
-        k = atomicCAS((unsigned long long*)(tk + s), 0ull, (unsigned long long)ek);
-        if (k == 0) k = ek;
-      }
-      if (k == ek) {
-        uint64_t* w = acc + (size_t)s * A * GB_BLOCK + threadIdx.x;
-#pragma unroll
-        for (int a = 0; a < A; ++a) {
-          if (a < p.n_aggs) {
-            uint64_t o = w[a * GB_BLOCK];
-            w[a * GB_BLOCK] = ((p.umax_mask >> a) & 1u) ? (o > x[a] ? o : x[a]) : o + x[a];
-          }
-        }
-        return;
-      }
-      s = (s + 1) & (TINY_SLOTS - 1);
-    }
-    gtab_update<A>(p, ek, x);
-  }
-  __device__ void flush(const GbParams& p) {
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int pr = warp; pr < TINY_SLOTS * A; pr += GB_BLOCK / 32) {
-      const int s = pr / A, a = pr % A;
-      if (tk[s] == 0 || a >= p.n_aggs) continue;
-      const bool um = (p.umax_mask >> a) & 1u;
-      const uint64_t* w = acc + ((size_t)s * A + a) * GB_BLOCK;
-      uint64_t v = 0;
-      for (int t = lane; t < GB_BLOCK; t += 32) {
-        uint64_t y = w[t];
-        v = um ? (v > y ? v : y) : v + y;
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        uint64_t y = __shfl_xor_sync(0xffffffffu, v, o);
-        v = um ? (v > y ? v : y) : v + y;
-      }
-      if (lane == 0) res[s * A + a] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < TINY_SLOTS && tk[threadIdx.x] != 0) {
-      uint64_t x[A];
-#pragma unroll
-      for (int a = 0; a < A; ++a) x[a] = res[threadIdx.x * A + a];
-      gtab_update<A>(p, tk[threadIdx.x], x);
-    }
-  }
-};
+// Thread-private -> CTA-shared -> global, each layer optional.  Only the
+// GB_BLOCK consumer threads call these.
+template <class S>
+struct BeLayered {
+  static constexpr int A = S::A;
+  static constexpr int ID = relhost::K_GB_LAYERED;
+  uint64_t* tk;              // [tiny_slots] stored keys
+  uint64_t* tacc;            // [tiny_slots][A][GB_BLOCK] thread-private words
+  uint64_t* tres;            // [tiny_slots][A] reduced words (flush)
+  uint64_t* sk;              // [smem_slots] stored keys
+  unsigned long long* sacc;  // [smem_slots][A]
 
-// CTA-shared table of smem_slots keys with shared-memory atomics.
-template <int A>
-struct BeShared {
-  static constexpr int ID = relhost::K_GB_SHARED;
-  uint64_t* tk;
-  unsigned long long* acc;
-  uint32_t mask;
-  __host__ __device__ static uint64_t bytes(int, uint32_t slots) {
-    return 8ull * slots * (1 + A);
+  __host__ __device__ static uint64_t bytes(uint32_t tiny, uint32_t shared) {
+    return 8ull * tiny * (1 + (uint64_t)A * GB_BLOCK + A) + 8ull * shared * (1 + A);
   }
   __device__ void bind(uint8_t* area, const GbParams& p) {
     tk = (uint64_t*)area;
-    acc = (unsigned long long*)(tk + p.smem_slots);
-    mask = p.smem_slots - 1;
+    tacc = tk + p.tiny_slots;
+    tres = tacc + (size_t)p.tiny_slots * A * GB_BLOCK;
+    sk = tres + (size_t)p.tiny_slots * A;
+    sacc = (unsigned long long*)(sk + p.smem_slots);
   }
   __device__ void init(const GbParams& p) {
-    for (uint32_t i = threadIdx.x; i < p.smem_slots * (1 + A); i += GB_BLOCK) tk[i] = 0;
+    const uint32_t n1 = p.tiny_slots * (1 + A * GB_BLOCK);
+    for (uint32_t i = threadIdx.x; i < n1; i += GB_BLOCK) tk[i] = 0;
+    const uint32_t n2 = p.smem_slots * (1 + A);
+    for (uint32_t i = threadIdx.x; i < n2; i += GB_BLOCK) sk[i] = 0;
   }
-  __device__ __forceinline__ void update(const GbParams& p, uint64_t ek, const uint64_t (&x)[A]) {
-    uint32_t s = small_slot_of(ek, mask);
-#pragma unroll 1
-    for (int i = 0; i < SHARED_PROBES; ++i) {
-      uint64_t k = *(volatile uint64_t*)(tk + s);
-      if (k == 0) {
-        k = atomicCAS((unsigned long long*)(tk + s), 0ull, (unsigned long long)ek);
-        if (k == 0) k = ek;
-      }
-      if (k == ek) {
-        unsigned long long* w = acc + (size_t)s * A;
+  __device__ __forceinline__ void tiny_rmw(const GbParams& p, uint32_t s, const Vals<A>& x) {
+    uint64_t* w = tacc + (size_t)s * A * GB_BLOCK + threadIdx.x;
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
-          if (a < p.n_aggs) {
-            if ((p.umax_mask >> a) & 1u)
-              atomicMax(w + a, (unsigned long long)x[a]);
-            else
-              atomicAdd(w + a, (unsigned long long)x[a]);
-          }
-        }
-        return;
+    for (int a = 0; a < A; ++a) {
+      if (live_agg<S>(p, a)) {
+        const uint64_t o = w[a * GB_BLOCK];
+        w[a * GB_BLOCK] = is_umax<S>(p, a) ? (o > x.v[a] ? o : x.v[a]) : o + x.v[a];
       }
-      s = (s + 1) & mask;
     }
-    gtab_update<A>(p, ek, x);
+  }
+  // Find the slot first, then update once: lanes that found their key at
+  // different probe depths reconverge before the (long) update sequence.
+  // false only when the global table overflowed.
+  __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>& x) {
+    int where = 0;  // 1: thread-private slot s, 2: CTA-shared slot s, 0: neither
+    uint32_t s = 0;
+    if (p.tiny_slots) {
+      const uint32_t mask = p.tiny_slots - 1;
+      s = small_slot_of(ek, mask, TINY_MULT);
+#pragma unroll 1
+      for (uint32_t i = 0; i < p.tiny_probes; ++i) {
+        uint64_t k = *(volatile uint64_t*)(tk + s);
+        if (k == 0) {
+          k = atomicCAS((unsigned long long*)(tk + s), 0ull, (unsigned long long)ek);
+          if (k == 0) k = ek;
+        }
+        if (k == ek) {
+          where = 1;
+          break;
+        }
+        s = (s + 1) & mask;
+      }
+    }
+    if (where == 0 && p.smem_slots) {
+      const uint32_t mask = p.smem_slots - 1;
+      s = small_slot_of(ek, mask, SHARED_MULT);
+#pragma unroll 1
+      for (uint32_t i = 0; i < p.shared_probes; ++i) {
+        uint64_t k = *(volatile uint64_t*)(sk + s);
+        if (k == 0) {
+          k = atomicCAS((unsigned long long*)(sk + s), 0ull, (unsigned long long)ek);
+          if (k == 0) k = ek;
+        }
+        if (k == ek) {
+          where = 2;
+          break;
+        }
+        s = (s + 1) & mask;
+      }
+    }
+    if (where == 1) {
+      tiny_rmw(p, s, x);
+      return true;
+    }
+    if (where == 2) {
+      red_words<S>(p, sacc + (size_t)s * A, x);
+      return true;
+    }
+    if (p.tiny_slots || p.smem_slots) return gtab_update<S>(p, ek, x);
+    return gtab_update_inl<S>(p, ek, x);
   }
   __device__ void flush(const GbParams& p) {
-    __syncthreads();
-    for (uint32_t s = threadIdx.x; s < p.smem_slots; s += GB_BLOCK) {
-      uint64_t k = tk[s];
-      if (k == 0) continue;
-      uint64_t x[A];
+    named_sync(GB_BLOCK);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p.tiny_slots) {
+      for (uint32_t pr = warp; pr < p.tiny_slots * A; pr += GB_BLOCK / 32) {
+        const uint32_t s = pr / A, a = pr % A;
+        if (tk[s] == 0 || !live_agg<S>(p, a)) continue;
+        const bool um = is_umax<S>(p, a);
+        const uint64_t* w = tacc + ((size_t)s * A + a) * GB_BLOCK;
+        uint64_t v = 0;
+        for (int t = lane; t < GB_BLOCK; t += 32) {
+          const uint64_t y = w[t];
+          v = um ? (v > y ? v : y) : v + y;
+        }
 #pragma unroll
-      for (int a = 0; a < A; ++a) x[a] = acc[(size_t)s * A + a];
-      gtab_update<A>(p, k, x);
+        for (int o = 16; o; o >>= 1) {
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, v, o);
+          v = um ? (v > y ? v : y) : v + y;
+        }
+        if (lane == 0) tres[s * A + a] = v;
+      }
+      named_sync(GB_BLOCK);
+      if (threadIdx.x < p.tiny_slots && tk[threadIdx.x] != 0) {
+        Vals<A> x;
+#pragma unroll
+        for (int a = 0; a < A; ++a) x.v[a] = tres[threadIdx.x * A + a];
+        gtab_update<S>(p, tk[threadIdx.x], x);
+      }
+    }
+    for (uint32_t s = threadIdx.x; s < p.smem_slots; s += GB_BLOCK) {
+      const uint64_t k = sk[s];
+      if (k == 0) continue;
+      Vals<A> x;
+#pragma unroll
+      for (int a = 0; a < A; ++a) x.v[a] = sacc[(size_t)s * A + a];
+      gtab_update<S>(p, k, x);
     }
   }
 };
 
 // Distinct-key counting: a CTA-shared key filter in front of the global set.
-template <int A>
+template <class S>
 struct BeKeySet {
+  static constexpr int A = S::A;
   static constexpr int ID = relhost::K_GB_KEYSET;
   uint64_t* tk;
-  uint32_t mask;
-  __host__ __device__ static uint64_t bytes(int, uint32_t slots) { return 8ull * slots; }
-  __device__ void bind(uint8_t* area, const GbParams& p) {
-    tk = (uint64_t*)area;
-    mask = p.smem_slots - 1;
-  }
+  __host__ __device__ static uint64_t bytes(uint32_t, uint32_t shared) { return 8ull * shared; }
+  __device__ void bind(uint8_t* area, const GbParams&) { tk = (uint64_t*)area; }
   __device__ void init(const GbParams& p) {
     for (uint32_t i = threadIdx.x; i < p.smem_slots; i += GB_BLOCK) tk[i] = 0;
   }
-  __device__ __forceinline__ void update(const GbParams& p, uint64_t ek, const uint64_t (&)[A]) {
-    uint32_t s = small_slot_of(ek, mask);
-#pragma unroll 1
-    for (int i = 0; i < SHARED_PROBES; ++i) {
+  __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>&) {
+    const uint32_t mask = p.smem_slots - 1;
+    uint32_t s = small_slot_of(ek, mask, SHARED_MULT);
+    for (uint32_t i = 0; i < p.shared_probes; ++i) {
       uint64_t k = *(volatile uint64_t*)(tk + s);
-      if (k == ek) return;  // this CTA already sent the key to the global set
+      if (k == ek) return true;  // this CTA already sent the key to the global set
       if (k == 0) {
         k = atomicCAS((unsigned long long*)(tk + s), 0ull, (unsigned long long)ek);
         if (k == 0) break;  // first sight in this CTA
-        if (k == ek) return;
+        if (k == ek) return true;
       }
       s = (s + 1) & mask;
     }
-    gset_insert(p, ek);
+    return gset_insert(p, ek);
   }
   __device__ void flush(const GbParams&) {}
 };
 
 // -------------------------------------------------------------- main kernel
 
-template <class Shape, class BE, int A, bool KEYSET, class V>
-__device__ __forceinline__ void run_rows(const GbParams& p, BE& be, const V& v, int nrows) {
-#pragma unroll 2
+// Fold rows [0, nrows) of a tile view into the backend; returns false once
+// the global table overflowed (later rows are then pointless).
+template <class S, class BE, bool KEYSET, class V>
+__device__ __forceinline__ bool run_rows(const GbParams& p, BE& be, const V& v, int nrows) {
+  bool ok = true;
+  const auto q = S::prep(p, v);
+#pragma unroll 4
   for (int r = threadIdx.x; r < nrows; r += GB_BLOCK) {
     uint64_t ek;
-    uint64_t x[A];
-    if (!Shape::template row<A>(p, v, r, ek, x)) continue;
+    Vals<S::A> x;
+    if (!S::row(p, q, r, ek, x)) continue;
     if (ek == 0) {  // the key INT64_MIN: side accumulator
-      if (KEYSET)
-        atomicAdd(&p.hdr->n_side, 1ull);
-      else
-        side_update<A>(p, x);
+      atomicAdd(&p.hdr->n_side, 1ull);
+      if (!KEYSET) red_words<S>(p, p.hdr->side_aggs, x);
       continue;
     }
-    be.update(p, ek, x);
+    ok &= be.update(p, ek, x);
   }
+  return ok;
 }
 
-template <class Shape, class BE, int A, bool KEYSET, bool USE_TMA>
-__global__ void __launch_bounds__(GB_BLOCK) gb_main(const __grid_constant__ GbParams p) {
+// Persistent, warp-specialised: warps 0..7 consume (GB_BLOCK threads), warp 8
+// produces.  The producer streams tile after tile of every column into a
+// ring of n_stages shared-memory stages with TMA bulk copies; stage s is
+// "full" when its bytes have landed (full[s]) and "empty" again when all
+// eight consumer warps have arrived on empty[s].  No CTA-wide barrier runs
+// per tile.  Every wait is bounded; a wait that gives up sets hdr->timeout.
+template <class S, class BE, bool KEYSET, bool USE_TMA>
+__global__ void __launch_bounds__(GB_THREADS) gb_main(const __grid_constant__ GbParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
-  uint64_t* full = (uint64_t*)smem;  // GB_STAGES mbarriers
+  uint64_t* full = (uint64_t*)smem;        // [n_stages]
+  uint64_t* empty = (uint64_t*)smem + 8;   // [n_stages]
+  int* abort_flag = (int*)(smem + 120);
   uint8_t* area = smem + 128;
   BE be;
   be.bind(area, p);
-  be.init(p);
-  uint8_t* stages = area + ((BE::bytes(p.n_aggs, p.smem_slots) + 127) & ~127ull);
+  const bool consumer = threadIdx.x < GB_BLOCK;
+  if (consumer) be.init(p);
+  uint8_t* stages = area + ((BE::bytes(p.tiny_slots, p.smem_slots) + 127) & ~127ull);
 
   const int64_t T = p.tile_rows;
+  const int NS = p.n_stages;
   const int64_t n_tiles = USE_TMA ? p.n_rows / T : (p.n_rows + T - 1) / T;
   const int64_t mine = n_tiles > (int64_t)blockIdx.x
                            ? (n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1
                            : 0;
-  uint64_t policy = 0;
-  if (USE_TMA && threadIdx.x == 0) {
-    for (int s = 0; s < GB_STAGES; ++s) mbar_init(&full[s], 1);
-    fence_mbar_init();
-    policy = l2_evict_first_policy();
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    if (USE_TMA) {
+      for (int s = 0; s < NS; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], GB_BLOCK / 32);
+      }
+      fence_mbar_init();
+    }
   }
   __syncthreads();
 
-  auto issue = [&](int64_t k, int s) {
-    const int64_t t = (int64_t)blockIdx.x + k * (int64_t)gridDim.x;
-    mbar_arrive_expect_tx(&full[s], p.stage_bytes);
-    uint8_t* dst = stages + (size_t)s * p.stage_bytes;
-    for (int c = 0; c < p.n_cols; ++c) {
-      const uint32_t nb = (uint32_t)(T * p.csize[c]);
-      bulk_g2s(dst + p.stage_off[c], p.col[c] + t * T * p.csize[c], nb, &full[s], policy);
-    }
-  };
-
-  bool stopped = false;
-  if (USE_TMA) {
-    if (threadIdx.x == 0)
-      for (int64_t k = 0; k < mine && k < GB_STAGES; ++k) issue(k, (int)k);
+  if (!consumer) {
+    // ---- producer warp: one lane issues every copy of this CTA
+    if (!USE_TMA || (threadIdx.x & 31) != 0) return;
+    const uint64_t policy = l2_evict_first_policy();
     int64_t k = 0;
     for (; k < mine; ++k) {
-      const int s = (int)(k % GB_STAGES);
-      const uint32_t par = (uint32_t)((k / GB_STAGES) & 1);
-      const bool ok = mbar_wait_bounded(&full[s], par, WAIT_LIMIT_NS);
-      if (ok)
-        run_rows<Shape, BE, A, KEYSET>(p, be, SmemView{stages + (size_t)s * p.stage_bytes}, (int)T);
-      else
+      const int s = (int)(k % NS);
+      if (k >= NS &&
+          !mbar_wait_bounded(&empty[s], (uint32_t)((k / NS - 1) & 1), WAIT_LIMIT_NS)) {
         atomicOr(&p.hdr->timeout, 1u);
-      int stop = !ok;
-      if (threadIdx.x == 0) stop |= ld_relaxed_u32(&p.hdr->overflow) != 0;
-      if (__syncthreads_or(stop)) {
-        stopped = true;
         break;
       }
-      if (threadIdx.x == 0 && k + GB_STAGES < mine) issue(k + GB_STAGES, s);
+      if (*(volatile int*)abort_flag) break;
+      const int64_t t = (int64_t)blockIdx.x + k * (int64_t)gridDim.x;
+      mbar_arrive_expect_tx(&full[s], p.stage_bytes);
+      uint8_t* dst = stages + (size_t)s * p.stage_bytes;
+      for (int c = 0; c < p.n_cols; ++c) {
+        const uint32_t nb = (uint32_t)(T * p.csize[c]);
+        bulk_g2s(dst + p.stage_off[c], p.col[c] + t * T * p.csize[c], nb, &full[s], policy);
+      }
     }
-    if (stopped) {
-      // let the copies already issued land before the CTA's shared memory goes away
-      if (threadIdx.x == 0)
-        for (int64_t j = k + 1; j < mine && j < k + GB_STAGES; ++j)
-          mbar_wait_bounded(&full[j % GB_STAGES], (uint32_t)((j / GB_STAGES) & 1), WAIT_LIMIT_NS);
-      __syncthreads();
-      return;
+    // the CTA's shared memory must outlive every copy issued into it
+    for (int64_t j = (k > NS ? k - NS : 0); j < k; ++j)
+      mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), WAIT_LIMIT_NS);
+    return;
+  }
+
+  // ---- consumers
+  const int lane = threadIdx.x & 31;
+  bool live = true;  // false once the global table overflowed
+  if (USE_TMA) {
+    for (int64_t k = 0; k < mine; ++k) {
+      const int s = (int)(k % NS);
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / NS) & 1), WAIT_LIMIT_NS)) {
+        atomicOr(&p.hdr->timeout, 1u);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (live) live = run_rows<S, BE, KEYSET>(p, be, SmemView{stages + (size_t)s * p.stage_bytes}, (int)T);
+      if ((k & 31) == 31) {  // now and then, notice another CTA's overflow
+        uint32_t f = lane == 0 ? ld_relaxed_u32(&p.hdr->overflow) : 0;
+        live = live && __shfl_sync(0xffffffffu, f, 0) == 0;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
     }
-    // rows after the last full tile: one CTA, straight from global memory
     const int64_t tail0 = n_tiles * T;
-    if (tail0 < p.n_rows && blockIdx.x == (unsigned)(n_tiles % gridDim.x))
-      run_rows<Shape, BE, A, KEYSET>(p, be, GlobalView{tail0}, (int)(p.n_rows - tail0));
+    if (live && tail0 < p.n_rows && blockIdx.x == (unsigned)(n_tiles % gridDim.x))
+      run_rows<S, BE, KEYSET>(p, be, GlobalView{tail0}, (int)(p.n_rows - tail0));
   } else {
     for (int64_t k = 0; k < mine; ++k) {
       const int64_t t = (int64_t)blockIdx.x + k * (int64_t)gridDim.x;
       const int64_t r0 = t * T;
       const int nrows = (int)(p.n_rows - r0 < T ? p.n_rows - r0 : T);
-      run_rows<Shape, BE, A, KEYSET>(p, be, GlobalView{r0}, nrows);
-      int stop = 0;
-      if (threadIdx.x == 0) stop = ld_relaxed_u32(&p.hdr->overflow) != 0;
-      if (__syncthreads_or(stop)) return;
+      const bool ok = run_rows<S, BE, KEYSET>(p, be, GlobalView{r0}, nrows);
+      uint32_t f = lane == 0 ? ld_relaxed_u32(&p.hdr->overflow) : 0;
+      f = __shfl_sync(0xffffffffu, f, 0);
+      if (!__all_sync(0xffffffffu, ok) || f) break;  // warp-uniform exit
     }
   }
+  // flush unless the result is void anyway (uniform across consumers)
+  named_sync(GB_BLOCK);
+  if (*(volatile int*)abort_flag) return;
   be.flush(p);
 }
 
@@ -537,72 +627,114 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_compact(const __grid_constant__ G
 
 // ------------------------------------------------------------------ launch
 
-int gb_shape_width(int shape) {
-  return shape == SHAPE_Q1 ? 5 : (shape == SHAPE_KV64 || shape == SHAPE_KV32) ? 4 : REL_MAX_AGGS;
-}
-
-uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t smem_slots) {
-  const uint64_t A = (uint64_t)gb_shape_width(shape);
-  switch (mode) {
-    case MODE_TINY: return 8ull * (TINY_SLOTS + TINY_SLOTS * A * GB_BLOCK + TINY_SLOTS * A);
-    case MODE_SHARED: return 8ull * smem_slots * (1 + A);
-    case MODE_KEYSET: return 8ull * smem_slots;
-    default: return 0;
-  }
-}
-
 namespace {
 
-template <class Shape, class BE, int A, bool KEYSET, bool TMA>
+template <class F>
+auto with_shape(int shape, F&& f) {
+  switch (shape) {
+    case SHAPE_Q1: return f(ShapeQ1{});
+    case SHAPE_KVRT64: return f(ShapeKVRT<int64_t>{});
+    case SHAPE_KVRT32: return f(ShapeKVRT<int32_t>{});
+    case SHAPE_KV4_64: return f(ShapeKV<int64_t, 4>{});
+    case SHAPE_KV4_32: return f(ShapeKV<int32_t, 4>{});
+    case SHAPE_KV2_64: return f(ShapeKV<int64_t, 2>{});
+    case SHAPE_KV2_32: return f(ShapeKV<int32_t, 2>{});
+    default: return f(ShapeGeneric{});
+  }
+}
+
+// The key-set pass only needs keys and filters: it runs on a reduced
+// descriptor, so fewer shapes are instantiated for it.
+template <class F>
+auto with_keyset_shape(int shape, F&& f) {
+  switch (shape) {
+    case SHAPE_Q1: return f(ShapeQ1{});
+    case SHAPE_KVRT64: case SHAPE_KV4_64: case SHAPE_KV2_64: return f(ShapeKVRT<int64_t>{});
+    case SHAPE_KVRT32: case SHAPE_KV4_32: case SHAPE_KV2_32: return f(ShapeKVRT<int32_t>{});
+    default: return f(ShapeGeneric{});
+  }
+}
+
+template <class S, class BE, bool KEYSET, bool TMA>
+size_t smem_of(const GbParams& p) {
+  const uint64_t be = (BE::bytes(p.tiny_slots, p.smem_slots) + 127) & ~127ull;
+  return 128 + be + (TMA ? (size_t)p.n_stages * p.stage_bytes : 0);
+}
+
+template <class S, class BE, bool KEYSET, bool TMA>
+int occupancy(const GbParams& p) {
+  auto kern = gb_main<S, BE, KEYSET, TMA>;
+  const size_t smem = smem_of<S, BE, KEYSET, TMA>(p);
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GB_THREADS, smem) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+template <class S, class BE, bool KEYSET, bool TMA>
 rel_status launch_one(const GbParams& p, cudaStream_t st) {
-  auto kern = gb_main<Shape, BE, A, KEYSET, TMA>;
-  const uint64_t be_bytes = (BE::bytes(p.n_aggs, p.smem_slots) + 127) & ~127ull;
-  const size_t smem = 128 + be_bytes + (TMA ? (size_t)GB_STAGES * p.stage_bytes : 0);
-  if (smem > 227 * 1024) {
-    relhost::set_error("group-by: %zu bytes of shared memory exceed the limit", smem);
+  auto kern = gb_main<S, BE, KEYSET, TMA>;
+  const size_t smem = smem_of<S, BE, KEYSET, TMA>(p);
+  const int per_sm = occupancy<S, BE, KEYSET, TMA>(p);
+  if (per_sm < 1) {
+    relhost::set_error("group-by: %zu bytes of shared memory per CTA cannot launch", smem);
     return REL_E_UNSUPPORTED;
   }
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(group-by)");
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GB_BLOCK, smem);
-  if (e != cudaSuccess) return relhost::cuda_fail(e, "occupancy(group-by)");
-  if (per_sm < 1) per_sm = 1;
   const int64_t tiles = (p.n_rows + p.tile_rows - 1) / p.tile_rows;
   int64_t grid = (int64_t)relhost::device_sms() * per_sm;
   if (grid > tiles) grid = tiles > 0 ? tiles : 1;
   relhost::launch_begin(BE::ID, st);
-  kern<<<(unsigned)grid, GB_BLOCK, smem, st>>>(p);
+  kern<<<(unsigned)grid, GB_THREADS, smem, st>>>(p);
   relhost::launch_end(BE::ID, st);
-  e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return relhost::cuda_fail(e, "launch(group-by)");
   return REL_OK;
 }
 
-template <class Shape, int A>
-rel_status launch_mode(const GbParams& p, int mode, bool tma, cudaStream_t st) {
-#define REL_GB_CASE(BE, KS)                                                         \
-  return tma ? launch_one<Shape, BE<A>, A, KS, true>(p, st)                         \
-             : launch_one<Shape, BE<A>, A, KS, false>(p, st)
-  switch (mode) {
-    case MODE_TINY: REL_GB_CASE(BeTiny, false);
-    case MODE_SHARED: REL_GB_CASE(BeShared, false);
-    case MODE_KEYSET: REL_GB_CASE(BeKeySet, true);
-    default: REL_GB_CASE(BeGlobal, false);
-  }
-#undef REL_GB_CASE
-}
-
 }  // namespace
 
-rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool use_tma, cudaStream_t st) {
+int gb_shape_width(int shape) {
+  return with_shape(shape, [](auto s) { return decltype(s)::A; });
+}
+
+uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t tiny_slots, uint32_t smem_slots) {
+  if (mode == MODE_KEYSET) return 8ull * smem_slots;
+  return with_shape(shape, [&](auto s) {
+    return BeLayered<decltype(s)>::bytes(tiny_slots, smem_slots);
+  });
+}
+
+int gb_ctas_per_sm(const GbParams& p, int shape, int mode, bool tma) {
+  if (mode == MODE_KEYSET)
+    return with_keyset_shape(shape, [&](auto s) {
+      using S = decltype(s);
+      return tma ? occupancy<S, BeKeySet<S>, true, true>(p)
+                 : occupancy<S, BeKeySet<S>, true, false>(p);
+    });
+  return with_shape(shape, [&](auto s) {
+    using S = decltype(s);
+    return tma ? occupancy<S, BeLayered<S>, false, true>(p)
+               : occupancy<S, BeLayered<S>, false, false>(p);
+  });
+}
+
+rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool tma, cudaStream_t st) {
   if (p.n_rows == 0) return REL_OK;
-  switch (shape) {
-    case SHAPE_Q1: return launch_mode<ShapeQ1, 5>(p, mode, use_tma, st);
-    case SHAPE_KV64: return launch_mode<ShapeKV<int64_t>, 4>(p, mode, use_tma, st);
-    case SHAPE_KV32: return launch_mode<ShapeKV<int32_t>, 4>(p, mode, use_tma, st);
-    default: return launch_mode<ShapeGeneric, REL_MAX_AGGS>(p, mode, use_tma, st);
-  }
+  if (mode == MODE_KEYSET)
+    return with_keyset_shape(shape, [&](auto s) {
+      using S = decltype(s);
+      return tma ? launch_one<S, BeKeySet<S>, true, true>(p, st)
+                 : launch_one<S, BeKeySet<S>, true, false>(p, st);
+    });
+  return with_shape(shape, [&](auto s) {
+    using S = decltype(s);
+    return tma ? launch_one<S, BeLayered<S>, false, true>(p, st)
+               : launch_one<S, BeLayered<S>, false, false>(p, st);
+  });
 }
 
 rel_status gb_launch_compact(const GbParams& p, const GbOut& o, cudaStream_t st) {
@@ -614,7 +746,7 @@ rel_status gb_launch_compact(const GbParams& p, const GbOut& o, cudaStream_t st)
   relhost::launch_begin(relhost::K_GB_COMPACT, st);
   gb_compact<<<(unsigned)grid, GB_BLOCK, 0, st>>>(p, o);
   relhost::launch_end(relhost::K_GB_COMPACT, st);
-  cudaError_t e = cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return relhost::cuda_fail(e, "launch(compact)");
   return REL_OK;
 }

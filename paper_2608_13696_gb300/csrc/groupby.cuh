@@ -6,13 +6,28 @@
 
 namespace rel {
 
-constexpr int GB_BLOCK = 256;
-constexpr int GB_STAGES = 3;
-constexpr int TINY_SLOTS = 8;
-constexpr int SHARED_PROBES = 16;
+constexpr int GB_BLOCK = 256;                // consumer threads per CTA
+constexpr int GB_THREADS = GB_BLOCK + 32;    // + one TMA producer warp
+constexpr int GB_MAX_STAGES = 4;
+constexpr int TINY_MAX_SLOTS = 32;
+constexpr int SHARED_MAX_SLOTS = 4096;
 
-enum GbMode : int { MODE_GLOBAL = 0, MODE_TINY = 1, MODE_SHARED = 2, MODE_KEYSET = 3 };
-enum GbShape : int { SHAPE_GENERIC = 0, SHAPE_Q1 = 1, SHAPE_KV64 = 2, SHAPE_KV32 = 3 };
+enum GbMode : int { MODE_LAYERED = 0, MODE_KEYSET = 1 };
+
+// Row shapes.  The specialised ones fix column types and aggregate kinds at
+// compile time; KV4 / KV2 hold their aggregates in the internal order
+// (sum, count, min, max) / (sum, count) and the host permutes the outputs.
+enum GbShape : int {
+  SHAPE_GENERIC = 0,
+  SHAPE_Q1 = 1,
+  SHAPE_KVRT64 = 2,  // runtime aggregate ops, int64 key
+  SHAPE_KVRT32 = 3,  // runtime aggregate ops, int32 key
+  SHAPE_KV4_64 = 4,  // sum, count, min, max of one int64 value; int64 key
+  SHAPE_KV4_32 = 5,
+  SHAPE_KV2_64 = 6,  // sum, count
+  SHAPE_KV2_32 = 7,
+  SHAPE_COUNT = 8
+};
 
 struct GbParams {
   int64_t n_rows;
@@ -23,6 +38,7 @@ struct GbParams {
   uint32_t stage_off[REL_MAX_COLS];  // byte offset of column c inside one stage
   uint32_t stage_bytes;              // bytes of one stage (all columns)
   int32_t tile_rows;                 // rows per tile, a multiple of 16
+  int32_t n_stages;                  // 2..GB_MAX_STAGES
   int32_t key_col[REL_MAX_KEYS];
   int32_t key_shift[REL_MAX_KEYS];
   uint64_t key_mask[REL_MAX_KEYS];
@@ -31,21 +47,25 @@ struct GbParams {
   int32_t aop[REL_MAX_AGGS], abase[REL_MAX_AGGS], anf[REL_MAX_AGGS];
   int32_t afcol[REL_MAX_AGGS][2];
   int64_t ac[REL_MAX_AGGS][2], as[REL_MAX_AGGS][2];
-  uint32_t umax_mask;  // bit a: aggregate a keeps an unsigned max (MIN / MAX)
+  uint32_t umax_mask;  // bit a: aggregate word a keeps an unsigned max (MIN / MAX)
   // roles of the specialised shapes
-  int32_t r_k0, r_k1, r_pred, r_a, r_b, r_d, r_t;  // Q1: keys, filter, sum cols, factor cols
+  int32_t r_k0, r_k1, r_pred, r_a, r_b, r_d, r_t;
+  // per-CTA layers
+  uint32_t tiny_slots;     // 0 or 8 / 16 / 32 thread-private slots
+  uint32_t tiny_probes;    // probes in the thread-private table before moving on
+  uint32_t smem_slots;     // 0 or a power of two <= SHARED_MAX_SLOTS (CTA-shared table)
+  uint32_t shared_probes;  // probes in the CTA-shared table before moving on
   // global table (or key set in MODE_KEYSET)
   uint64_t* tkeys;
   unsigned long long* taggs;  // slots x n_aggs words
   int32_t log2_slots;
   uint32_t max_probe;
-  uint32_t smem_slots;  // MODE_SHARED / MODE_KEYSET per-CTA table slots (power of two)
   WsHeader* hdr;
 };
 
 struct GbOut {
   int64_t* keys;
-  int64_t* aggs[REL_MAX_AGGS];
+  int64_t* aggs[REL_MAX_AGGS];  // in the kernel's aggregate order
   int64_t capacity;
 };
 
@@ -55,7 +75,9 @@ rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool use_tma,
 rel_status gb_launch_compact(const GbParams& p, const GbOut& o, cudaStream_t st);
 // Aggregate-array width the kernel for a shape is compiled with.
 int gb_shape_width(int shape);
-// Shared-memory bytes of a backend's per-CTA table (before the staging ring).
-uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t smem_slots);
+// Shared-memory bytes of the per-CTA tables (before the staging ring).
+uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t tiny_slots, uint32_t smem_slots);
+// Occupancy of a configured launch (CTAs per SM), or 0 when it cannot launch.
+int gb_ctas_per_sm(const GbParams& p, int shape, int mode, bool use_tma);
 
 }  // namespace rel

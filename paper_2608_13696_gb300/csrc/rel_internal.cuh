@@ -49,10 +49,11 @@ __device__ __forceinline__ uint64_t slot_of(uint64_t ek, int log2_slots) {
   return (ek * 0x9E3779B97F4A7C15ull) >> (64 - log2_slots);
 }
 
-// Secondary hash for small per-CTA tables (independent of slot_of's bits).
-__device__ __forceinline__ uint32_t small_slot_of(uint64_t ek, uint32_t mask) {
-  uint64_t h = ek * 0xD6E8FEB86659FD93ull;
-  return (uint32_t)(h >> 40) & mask;
+// Hash for the small per-CTA tables: the key folded to 32 bits, then 32-bit
+// multiplicative hashing (one IMAD) -- cheap, and independent of slot_of.
+__device__ __forceinline__ uint32_t small_slot_of(uint64_t ek, uint32_t mask, uint32_t mult) {
+  const uint32_t f = (uint32_t)ek ^ (uint32_t)(ek >> 32);
+  return __umulhi(f, mult) & mask;
 }
 
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
@@ -87,6 +88,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -135,6 +140,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Barrier among the first `count` threads of the CTA (named barrier 1).
+__device__ __forceinline__ void named_sync(uint32_t count) {
+  asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
 // ------------------------------------------------------------------ status
 
 // Device-visible status words at the start of every workspace.
@@ -163,15 +173,13 @@ int device_sms();
 
 // Kernel ids for launch counting and event timing.
 enum KernelId : int {
-  K_GB_GLOBAL = 0,
-  K_GB_TINY = 1,
-  K_GB_SHARED = 2,
-  K_GB_KEYSET = 3,
-  K_GB_COMPACT = 4,
-  K_JOIN_BUILD = 5,
-  K_JOIN_PROBE = 6,
-  K_JOIN_COUNT = 7,
-  K_COUNT_IDS = 8
+  K_GB_LAYERED = 0,
+  K_GB_KEYSET = 1,
+  K_GB_COMPACT = 2,
+  K_JOIN_BUILD = 3,
+  K_JOIN_PROBE = 4,
+  K_JOIN_COUNT = 5,
+  K_COUNT_IDS = 6
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

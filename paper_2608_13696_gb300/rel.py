@@ -68,11 +68,19 @@ class Plan(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int64), ("variant", ctypes.c_int32),
                 ("smem_slots", ctypes.c_int32), ("workspace_bytes", ctypes.c_uint64),
                 ("scratch_bytes", ctypes.c_uint64), ("est_groups", ctypes.c_int64),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("tiny_slots", ctypes.c_int32)]
 
     def __repr__(self):
-        return (f"Plan(slots={self.slots}, variant={self.variant}, smem_slots={self.smem_slots}, "
-                f"workspace_bytes={self.workspace_bytes}, est_groups={self.est_groups})")
+        return (f"Plan(slots={self.slots}, variant={self.variant}, tiny_slots={self.tiny_slots}, "
+                f"smem_slots={self.smem_slots}, workspace_bytes={self.workspace_bytes}, "
+                f"est_groups={self.est_groups})")
+
+    def layers(self, tiny: int, smem: int, variant: int | None = None) -> "Plan":
+        """Set the per-CTA layers (thread-private slots, CTA-shared slots)."""
+        self.tiny_slots, self.smem_slots = tiny, smem
+        if variant is not None:
+            self.variant = variant
+        return self
 
 
 class JoinTableC(ctypes.Structure):

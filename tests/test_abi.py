@@ -66,14 +66,15 @@ def test_plan_from_hint_is_host_only(L):
     assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 1000, None, 0,
                            ctypes.byref(plan), None) == rel.REL_OK
     assert plan.est_groups == 1000 and plan.slots == 2048
-    assert plan.variant == rel.VAR_SMEM and plan.smem_slots == 2048
+    assert plan.variant == rel.VAR_SMEM and plan.smem_slots == 2048 and plan.tiny_slots == 8
     assert plan.workspace_bytes == L.rel_groupby_ws_bytes(2048, 1)
     assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 5, None, 0,
                            ctypes.byref(plan), None) == rel.REL_OK
-    assert plan.smem_slots == 8  # thread-private accumulators
+    assert plan.tiny_slots == 8 and plan.smem_slots == 0  # thread-private accumulators only
     assert L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), 0, 10**7, None, 0,
                            ctypes.byref(plan), None) == rel.REL_OK
     assert plan.variant == rel.VAR_GLOBAL and plan.slots == 1 << 25
+    assert plan.tiny_slots == 8 and plan.smem_slots == 2048  # caches in front of the table
 
 
 def test_exact_plan_reports_scratch_without_gpu(L):
@@ -125,6 +126,10 @@ def test_groupby_agg_argument_checks(L):
     assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
                              ctypes.byref(n), None) == rel.REL_E_INVALID
     plan.smem_slots = 0
+    plan.tiny_slots = 12
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
+                             ctypes.byref(n), None) == rel.REL_E_INVALID
+    plan.tiny_slots = 0
     # workspace too small: capacity error before any device work
     assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 100, 0x10, None, 0,
                              ctypes.byref(n), None) == rel.REL_E_CAPACITY

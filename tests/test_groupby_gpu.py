@@ -19,7 +19,9 @@ from test_oracle_groupby import rand_query
 
 pytestmark = pytest.mark.gpu
 
-MODES = {"tiny": (8, rel.VAR_SMEM), "shared": (256, rel.VAR_SMEM), "global": (0, rel.VAR_GLOBAL)}
+# per-CTA layers: (thread-private slots, CTA-shared slots, variant label)
+MODES = {"tiny": (8, 0, rel.VAR_SMEM), "shared": (0, 256, rel.VAR_SMEM),
+         "global": (0, 0, rel.VAR_GLOBAL), "layered": (8, 1024, rel.VAR_GLOBAL)}
 
 
 def gpu_groupby(q_np, mode=None, flags=0, hint=0, plan=None):
@@ -27,7 +29,7 @@ def gpu_groupby(q_np, mode=None, flags=0, hint=0, plan=None):
     if plan is None:
         plan = rel.plan_groupby(qc, flags=flags, groups_hint=hint)
     if mode is not None:
-        plan.smem_slots, plan.variant = MODES[mode]
+        plan.layers(*MODES[mode])
     plan.flags |= flags & rel.PLAN_GENERIC
     k, a = rel.groupby(qc, plan=plan)
     torch.cuda.synchronize()
@@ -55,7 +57,7 @@ def test_lineitem_full_exact_plan():
     li = synth.lineitem(1_000_000, seed=0)
     q = oracle.lineitem_query(li)
     plan = rel.plan_groupby(query_to_cuda(q), flags=rel.PLAN_EXACT)
-    assert plan.est_groups == 6 and plan.smem_slots == 8
+    assert plan.est_groups == 6 and plan.tiny_slots == 8 and plan.smem_slots == 0
     assert_same(q, gpu_groupby(q, plan=plan))
 
 
@@ -136,7 +138,7 @@ def test_misaligned_columns_take_the_unstaged_path():
     qc["cols"] = [c[1:] for c in qc["cols"]]  # 8-byte aligned, not 16
     for mode in MODES:
         plan = rel.plan_groupby(qc, groups_hint=5000)
-        plan.smem_slots, plan.variant = MODES[mode]
+        plan.layers(*MODES[mode])
         k, a = rel.groupby(qc, plan=plan)
         gk, ga = canon_groupby(k, a)
         ek, ea = oracle.groupby(q)
@@ -159,7 +161,7 @@ def test_overflow_is_reported_not_hung():
     keys, vals = synth.zipf_kv(100_000, seed=9, n_ranks=20_000)
     qc = query_to_cuda(oracle.kv_query(keys, vals))
     plan = rel.plan_groupby(qc, groups_hint=8)  # 16 slots for ~9000 groups
-    plan.smem_slots, plan.variant = 0, rel.VAR_GLOBAL
+    plan.layers(0, 0, rel.VAR_GLOBAL)
     with pytest.raises(rel.RelError) as e:
         rel.groupby(qc, plan=plan)
     assert e.value.status == rel.REL_E_OVERFLOW
@@ -209,4 +211,4 @@ def test_full_size_four_keys_200m():
     keys, vals = synth.few_keys_kv(N_BIG, n_keys=4, seed=0)
     sample = np.array([synth.mix64_signed(r) for r in (1, 2)])
     plan = _big_checks(keys, vals, rel.PLAN_EXACT, sample)
-    assert plan.est_groups == 4 and plan.smem_slots == 8
+    assert plan.est_groups == 4 and plan.tiny_slots == 8
