@@ -115,6 +115,9 @@ typedef struct {
 #define REL_PLAN_EXACT 1u   /* count distinct qualifying keys exactly (GPU pre-pass) */
 #define REL_PLAN_LEARNED 2u /* reserved: sample sketch + learned size / variant      */
 #define REL_PLAN_GENERIC 4u /* force the descriptor-interpreting kernel              */
+#define REL_PLAN_SKETCH 8u  /* sample sketch: heavy hitters pinned per CTA           */
+
+#define REL_MAX_HOT 32
 
 /* A plan fixes the table sizes; rows fall through thread-private slots, then
  * a CTA-shared table, then the global table (each of the first two optional),
@@ -130,6 +133,13 @@ typedef struct {
                                number of groups                                 */
   uint32_t flags;           /* REL_PLAN_* used                                  */
   int32_t tiny_slots;       /* thread-private slots per CTA: 0, 8, 16 or 32     */
+  uint32_t tiny_mult;       /* multiplier of the thread-private slot hash; 0
+                               picks the default                                */
+  int32_t n_hot;            /* > 0: these keys are preloaded into the thread-
+                               private slots, which then admit no other key     */
+  int64_t hot_keys[REL_MAX_HOT];
+  int32_t tile_rows;        /* rows per staged tile (256..2048, power of two); 0 = auto */
+  int32_t n_stages;         /* staging ring depth (2..8); 0 = auto                    */
 } rel_plan;
 
 #define REL_OP_GROUPBY 0
@@ -142,7 +152,13 @@ typedef struct {
  *      plan->scratch_bytes of ws (query with ws = NULL: returns
  *      REL_E_CAPACITY after filling scratch_bytes);
  *    otherwise: size for n_rows groups (always sufficient, rarely economical).
- *    Fills slots, variant, smem_slots, workspace_bytes, est_groups.
+ *    flags & REL_PLAN_SKETCH (with any of the above): also run rel_sketch and
+ *      pin the sample's most frequent keys in the thread-private slots (all
+ *      of them when the sample suggests few groups, the heavy hitters when it
+ *      is skewed), with a hash multiplier that places them without
+ *      collisions.  Needs rel_sketch_ws_bytes() of ws as well.
+ *    Fills slots, variant, tiny/smem slots, hot keys, workspace_bytes,
+ *    est_groups.
  *  op = REL_OP_JOIN_PROBE, desc = const rel_join_probe_desc*: counts the
  *    pairs the probe will emit (the paper's "count" step) into est_groups.
  *  Returns REL_OK, REL_E_INVALID, REL_E_CAPACITY, REL_E_CUDA, REL_E_TIMEOUT. */
@@ -169,6 +185,41 @@ rel_status rel_groupby_agg(const rel_groupby_desc* desc, const rel_plan* plan, v
 /* Device bytes rel_groupby_agg needs for `slots` table slots and `n_aggs`
  * aggregates. */
 uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs);
+
+/* ------------------------------------------------------ sample sketch */
+
+#define REL_SKETCH_TOP 32
+#define REL_SKETCH_FEATURES 264
+
+/* Summary of a 4096-row sample of a group-by input (the planner's view of
+ * the data; the paper has no planner, this is what the sizing step reads).
+ * Sample: every row when n_rows <= 4096, else 64 windows of 64 consecutive
+ * rows starting at floor(w * (n_rows - 64) / 63); rows the filter rejects
+ * are dropped ("kept" = the rest).  runs counts maximal runs of equal keys
+ * among kept rows inside each block of 64 sample positions.  hll holds 256
+ * HyperLogLog registers (p = 8) of splitmix64(key): register h >> 56, value
+ * = leading zeros of the low 56 bits + 1 (57 if zero).  top_* lists up to 32
+ * keys by count descending, key ascending.  features = hll / 57 followed by
+ * log2(n_rows), ndv / kept, log2(key_max - key_min + 1), top-1 share, top-8
+ * share, singletons / ndv, kept / runs, key width / 64. */
+typedef struct {
+  int64_t n_rows;
+  int32_t sample_rows, kept, ndv, singletons, runs, key_bits;
+  int64_t key_min, key_max;
+  int64_t top_key[REL_SKETCH_TOP];
+  int32_t top_count[REL_SKETCH_TOP];
+  uint8_t hll[256];
+  float features[REL_SKETCH_FEATURES];
+} rel_sketch_info;
+
+/* Device bytes rel_sketch needs in ws. */
+uint64_t rel_sketch_ws_bytes(void);
+
+/* One single-CTA kernel over the sample; fills *out (host) after a stream
+ * sync.  Returns REL_OK, REL_E_INVALID, REL_E_CAPACITY (ws too small),
+ * REL_E_CUDA. */
+rel_status rel_sketch(const rel_groupby_desc* desc, void* ws, size_t ws_bytes,
+                      rel_sketch_info* out, void* stream);
 
 /* Group-by without any device allocation, for callers that cannot allocate
  * device memory: an engine whose own pool owns all of the GPU's memory and

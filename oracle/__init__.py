@@ -59,6 +59,9 @@ def _L():
             lib.orc_join.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp]
             lib.orc_join_count.restype = i64
             lib.orc_join_count.argtypes = [vp, i64, vp, i64]
+            lib.orc_sketch.restype = None
+            lib.orc_sketch.argtypes = [i64, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp,
+                                       vp]
             _lib = lib
     return _lib
 
@@ -120,6 +123,63 @@ def groupby(q: dict):
     out_keys = _take(ok_p.value, ng, np.int64)
     out_aggs = _take(oa_p.value, ng * A, np.int64).reshape(A, ng)
     return out_keys, out_aggs
+
+
+def sketch(q: dict) -> dict:
+    """Sample summary (see orc_sketch) plus the 264 planner features computed
+    here in double precision from the integer summary."""
+    import math
+
+    cols = [np.ascontiguousarray(c) for c in q["cols"]]
+    n = len(cols[0])
+    ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+    types = _arr([_TYPES[c.dtype] for c in cols], np.int32)
+    keys = _arr(q["keys"], np.int32)
+    preds = q.get("preds", [])
+    pc = _arr([p[0] for p in preds], np.int32)
+    plo = _arr([p[1] for p in preds], np.int64)
+    phi = _arr([p[2] for p in preds], np.int64)
+    ints = np.zeros(5, np.int32)
+    mm = np.zeros(2, np.int64)
+    tk = np.zeros(32, np.int64)
+    tc = np.zeros(32, np.int32)
+    hll = np.zeros(256, np.uint8)
+    _L().orc_sketch(n, ptrs, types.ctypes.data, len(q["keys"]), keys.ctypes.data, len(preds),
+                    pc.ctypes.data, plo.ctypes.data, phi.ctypes.data, ints.ctypes.data,
+                    mm.ctypes.data, tk.ctypes.data, tc.ctypes.data, hll.ctypes.data)
+    s = dict(zip(["sample_rows", "kept", "ndv", "singletons", "runs"], ints.tolist()))
+    s.update(key_min=int(mm[0]), key_max=int(mm[1]), top_key=tk, top_count=tc, hll=hll)
+    bits = {np.dtype(np.uint8): 8, np.dtype(np.int32): 32, np.dtype(np.int64): 64}
+    s["key_bits"] = sum(bits[cols[k].dtype] for k in q["keys"])
+    kept, ndv = s["kept"], s["ndv"]
+    span = (s["key_max"] - s["key_min"]) % (1 << 64)
+    stats = [
+        math.log2(max(n, 1)),
+        ndv / kept if kept else 0.0,
+        math.log2(float(span) + 1.0) if kept else 0.0,
+        int(tc[0]) / kept if kept else 0.0,
+        int(tc[:8].sum()) / kept if kept else 0.0,
+        s["singletons"] / ndv if ndv else 0.0,
+        kept / s["runs"] if s["runs"] else 0.0,
+        s["key_bits"] / 64.0,
+    ]
+    s["features"] = np.array([h / 57.0 for h in hll.tolist()] + stats, dtype=np.float64)
+    return s
+
+
+def hll_estimate(registers) -> float:
+    """HyperLogLog cardinality estimate with the small-range (linear counting)
+    correction of Flajolet et al. (2007), m = number of registers."""
+    import math
+
+    r = np.asarray(registers, dtype=np.float64)
+    m = len(r)
+    alpha = 0.7213 / (1 + 1.079 / m)
+    e = alpha * m * m / np.sum(2.0 ** (-r))
+    zeros = int((r == 0).sum())
+    if e <= 2.5 * m and zeros:
+        e = m * math.log(m / zeros)
+    return float(e)
 
 
 def join(build_keys, payload, probe_keys):

@@ -204,6 +204,79 @@ int64_t orc_join(const int64_t* build_key, const int64_t* payload, int64_t n_bui
   return (int64_t)pi.size();
 }
 
+// Sample summary a planner reads before sizing a group-by (no counterpart in
+// the paper; its definition is stated with rel_sketch in include/rel.h):
+// the sample is every row when n_rows <= 4096, else rows
+// floor(w * (n_rows - 64) / 63) + o for w, o in [0, 64); filtered rows are
+// dropped.  Writes, in order: sample_rows, kept, ndv, singletons, runs into
+// ints[0..5); key_min, key_max into mm[0..2); top keys / counts (count
+// descending, key ascending, up to 32); the 256 HyperLogLog registers.
+void orc_sketch(int64_t n_rows, const void* const* col_data, const int32_t* col_type,
+                int32_t n_keys, const int32_t* key_cols, int32_t n_preds,
+                const int32_t* pred_col, const int64_t* pred_lo, const int64_t* pred_hi,
+                int32_t* ints, int64_t* mm, int64_t* top_key, int32_t* top_count,
+                uint8_t* hll) {
+  const int64_t S = n_rows < 4096 ? n_rows : 4096;
+  std::vector<int64_t> kept_keys;
+  std::vector<int> block;  // which block of 64 sample positions a kept key came from
+  for (int64_t j = 0; j < S; j++) {
+    const int64_t row = n_rows <= 4096 ? j : (j / 64) * (n_rows - 64) / 63 + (j % 64);
+    bool keep = true;
+    for (int32_t p = 0; p < n_preds && keep; p++) {
+      int64_t x = read_col(col_data[pred_col[p]], col_type[pred_col[p]], row);
+      keep = pred_lo[p] <= x && x <= pred_hi[p];
+    }
+    if (!keep) continue;
+    kept_keys.push_back(orc_group_key(row, n_keys, key_cols, col_data, col_type));
+    block.push_back((int)(j / 64));
+  }
+  std::memset(hll, 0, 256);
+  for (int64_t k : kept_keys) {
+    // splitmix64 output function of the key (Steele, Lea & Flood 2014)
+    uint64_t z = (uint64_t)k + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const int reg = (int)(z >> 56);
+    uint64_t rest = z << 8;  // the other 56 bits, at the top of the word
+    int rank = 1;
+    if (rest == 0) {
+      rank = 57;
+    } else {
+      while (!(rest >> 63)) {
+        rest <<= 1;
+        rank++;
+      }
+    }
+    if (rank > hll[reg]) hll[reg] = (uint8_t)rank;
+  }
+  std::unordered_map<int64_t, int32_t> count;
+  for (int64_t k : kept_keys) count[k] += 1;
+  int runs = 0;
+  for (size_t i = 0; i < kept_keys.size(); i++)
+    if (i == 0 || block[i] != block[i - 1] || kept_keys[i] != kept_keys[i - 1]) runs++;
+  int singles = 0;
+  std::vector<std::pair<int32_t, int64_t>> byfreq;
+  for (auto& kv : count) {
+    if (kv.second == 1) singles++;
+    byfreq.push_back({kv.second, kv.first});
+  }
+  std::sort(byfreq.begin(), byfreq.end(), [](const auto& a, const auto& b) {
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
+  });
+  for (int i = 0; i < 32; i++) {
+    top_key[i] = i < (int)byfreq.size() ? byfreq[(size_t)i].second : 0;
+    top_count[i] = i < (int)byfreq.size() ? byfreq[(size_t)i].first : 0;
+  }
+  ints[0] = (int32_t)S;
+  ints[1] = (int32_t)kept_keys.size();
+  ints[2] = (int32_t)count.size();
+  ints[3] = singles;
+  ints[4] = runs;
+  mm[0] = kept_keys.empty() ? 0 : *std::min_element(kept_keys.begin(), kept_keys.end());
+  mm[1] = kept_keys.empty() ? 0 : *std::max_element(kept_keys.begin(), kept_keys.end());
+}
+
 // Number of pairs the join above emits (the paper's "count" step).
 int64_t orc_join_count(const int64_t* build_key, int64_t n_build, const int64_t* probe_key,
                        int64_t n_probe) {

@@ -13,6 +13,9 @@
 
 #include "groupby.cuh"
 #include "join.cuh"
+#include "sketch.cuh"
+
+#include <cmath>
 
 // ------------------------------------------------------------ host helpers
 
@@ -334,20 +337,28 @@ bool configure_stages(GbParams& p, int shape, int mode, bool tma) {
     set_stages(p, 1024, 2);
     return cached_occupancy(p, shape, mode, false) > 0;
   }
+  if (p.req_tile && p.req_stages) {  // the plan (an autotuner) chose
+    const int t = p.req_tile, ns = p.req_stages;
+    set_stages(p, t, ns);
+    if (cached_occupancy(p, shape, mode, true) > 0) return true;
+  }
   uint64_t row_bytes = 0;
   for (int c = 0; c < p.n_cols; ++c) row_bytes += (uint64_t)p.csize[c];
   int best_t = 0, best_s = 0;
   long best_score = -1;
   for (int t : {2048, 1024, 512, 256}) {
-    for (int ns : {4, 3, 2}) {
+    for (int ns : {8, 6, 5, 4, 3, 2}) {
       if ((uint64_t)t * row_bytes > 48 * 1024) continue;
       set_stages(p, t, ns);
       const int occ = cached_occupancy(p, shape, mode, true);
       if (occ < 1) continue;
       const uint64_t inflight = (uint64_t)occ * ns * p.stage_bytes;
       const int warps = occ * (GB_BLOCK / 32);
-      const long score = (inflight >= 64 * 1024 ? 1000000L : 0L) +
-                         (long)(warps > 32 ? 32 : warps) * 1000 + (long)(t / 256) * 10 + ns;
+      // enough bytes in flight per SM to cover HBM latency (~96 KB), then as
+      // many resident warps as possible: the row loop is latency-bound
+      const uint64_t capped = inflight < 96 * 1024 ? inflight : 96 * 1024;
+      const long score = (long)(capped / 1024) * 100000L + (long)(warps > 48 ? 48 : warps) * 100 +
+                         (long)(t / 256) * 2 - ns;
       if (score > best_score) {
         best_score = score;
         best_t = t;
@@ -365,7 +376,13 @@ rel_status run_main(GbParams& p, int shape, int mode, cudaStream_t st) {
   const bool tma = tma_ok(p);
   for (;;) {
     if (configure_stages(p, shape, mode, tma)) return gb_launch_main(p, shape, mode, tma, st);
-    if (p.tiny_slots > 8) {
+    if (p.tiny_frozen) {  // pinned placement cannot shrink: drop the layer
+      mode = mode == MODE_TINY ? MODE_LAYERED : mode;
+      p.tiny_frozen = 0;
+      p.tiny_ns = 0;
+      p.tiny_slots = 0;
+      p.tiny_probes = 0;
+    } else if (p.tiny_slots > 8) {
       p.tiny_slots >>= 1;
       p.tiny_probes = p.tiny_probes > p.tiny_slots ? p.tiny_slots : p.tiny_probes;
     } else if (p.tiny_slots) {
@@ -410,14 +427,110 @@ void choose_layers(int64_t est, int words, rel_plan* plan) {
   }
 }
 
+constexpr uint32_t DEFAULT_TINY_MULT = 0x9E3779B1u;
+
+// Host copy of the device's per-CTA slot hash (rel_internal.cuh, small_slot_of).
+uint32_t host_small_slot(uint64_t ek, uint32_t mask, uint32_t mult) {
+  const uint32_t f = (uint32_t)ek ^ (uint32_t)(ek >> 32);
+  return (uint32_t)(((uint64_t)f * mult) >> 32) & mask;
+}
+
+// Place the hot keys at their hash slots; false on a collision.
+bool place_hot(const int64_t* keys, int n, uint32_t slots, uint32_t mult, uint64_t* table) {
+  for (uint32_t s = 0; s < slots; ++s) table[s] = 0;
+  for (int i = 0; i < n; ++i) {
+    const uint64_t ek = (uint64_t)keys[i] ^ KEY_FLIP;
+    const uint32_t s = host_small_slot(ek, slots - 1, mult);
+    if (table[s] != 0) return false;
+    table[s] = ek;
+  }
+  return true;
+}
+
+// A multiplier that places every hot key in its own slot (0 if none found).
+uint32_t perfect_mult(const int64_t* keys, int n, uint32_t slots) {
+  uint64_t table[TINY_MAX_SLOTS];
+  for (uint32_t i = 0; i < 4096; ++i) {
+    const uint32_t mult = (DEFAULT_TINY_MULT + i * 0x3C6EF372u) | 1u;
+    if (place_hot(keys, n, slots, mult, table)) return mult;
+  }
+  return 0;
+}
+
+// Thread-private slots a shape can afford (their shared memory grows with
+// the aggregate words).
+int32_t tiny_capacity(int words) {
+  return words <= 2 ? 32 : words <= 4 ? 16 : words <= 6 ? 8 : 0;
+}
+
+// Pin the sample's frequent keys: all of them when the plan keeps every group
+// thread-private, else the heavy hitters of a skewed sample.
+void apply_sketch(const rel_sketch_info& s, int words, rel_plan* plan) {
+  const int32_t cap = tiny_capacity(words);
+  if (cap == 0 || s.kept == 0) return;
+  int64_t top8 = 0;
+  for (int i = 0; i < 8; ++i) top8 += s.top_count[i];
+  const bool tiny_only = plan->tiny_slots && !plan->smem_slots;
+  int want = 0;
+  if (tiny_only) {
+    want = s.ndv < plan->tiny_slots ? s.ndv : plan->tiny_slots;
+  } else if (top8 * 20 >= (int64_t)s.kept) {  // top 8 keys hold >= 5 % of rows
+    plan->tiny_slots = cap;
+    for (int i = 0; i < REL_SKETCH_TOP && i < cap / 2; ++i)
+      if (s.top_count[i] >= 2) want = i + 1;
+  } else {
+    plan->tiny_slots = 0;  // no heavy hitters: a thread-private layer only costs
+    return;
+  }
+  int n = 0;
+  for (int i = 0; i < want; ++i)
+    if (s.top_key[i] != INT64_MIN) plan->hot_keys[n++] = s.top_key[i];
+  if (n == 0) return;
+  // the fewest slots with a collision-free placement: thread-private columns
+  // cost shared memory that the staging ring needs for bytes in flight
+  for (uint32_t slots = (uint32_t)next_pow2((uint64_t)(n < 2 ? 2 : n));
+       slots <= (uint32_t)plan->tiny_slots; slots <<= 1) {
+    const uint32_t mult = perfect_mult(plan->hot_keys, n, slots);
+    if (mult) {
+      plan->n_hot = n;
+      plan->tiny_mult = mult;
+      plan->tiny_slots = (int32_t)slots;
+      return;
+    }
+  }
+}
+
 // Probe limits of the per-CTA layers: a layer that must hold every group
-// scans it all; a cache in front of a larger layer gives up early.
-void set_layers(GbParams& p, const rel_plan* plan) {
+// scans it all; a cache in front of a larger layer gives up early.  Pinned
+// hot keys sit at their own hash slot, so one probe decides.
+rel_status set_layers(GbParams& p, const rel_plan* plan, int shape) {
   p.tiny_slots = (uint32_t)plan->tiny_slots;
   p.smem_slots = (uint32_t)plan->smem_slots;
   const bool tiny_only = p.tiny_slots && !p.smem_slots && plan->variant == REL_VAR_SMEM;
   p.tiny_probes = tiny_only ? p.tiny_slots : (p.tiny_slots ? 2u : 0u);
   p.shared_probes = plan->variant == REL_VAR_SMEM ? 16u : 4u;
+  p.tiny_mult = plan->tiny_mult ? (plan->tiny_mult | 1u) : DEFAULT_TINY_MULT;
+  p.tiny_frozen = 0;
+  if (plan->n_hot > 0 && p.tiny_slots) {
+    if (plan->n_hot > (int32_t)p.tiny_slots || plan->n_hot > REL_MAX_HOT ||
+        !place_hot(plan->hot_keys, plan->n_hot, p.tiny_slots, p.tiny_mult, p.tiny_init))
+      return set_error("group-by: the plan's hot keys collide under its multiplier"),
+             REL_E_INVALID;
+    p.tiny_frozen = 1;
+    p.tiny_probes = 1;
+    // few pinned keys, no CTA-shared layer, a shape of <= 5 words: keep the
+    // accumulators in registers (dense ids in slot order)
+    const bool regs_shape = shape == SHAPE_Q1 || shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 ||
+                            shape == SHAPE_KV2_64 || shape == SHAPE_KV2_32;
+    if (regs_shape && p.smem_slots == 0 && plan->n_hot <= 8 && p.tiny_slots <= 16) {
+      p.tiny_ns = plan->n_hot <= 4 ? 4u : 8u;
+      p.tiny_dense = 0;
+      uint64_t j = 0;
+      for (uint32_t s = 0; s < p.tiny_slots; ++s)
+        if (p.tiny_init[s]) p.tiny_dense |= (j++) << (4 * s);
+    }
+  }
+  return REL_OK;
 }
 
 rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint, void* ws,
@@ -506,6 +619,18 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
   plan->slots = (int64_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
   choose_layers(est, gb_shape_width(m.shape), plan);
   plan->workspace_bytes = gb_ws_bytes(plan->slots, d->n_aggs);
+  if ((flags & REL_PLAN_SKETCH) && d->n_rows > 0) {
+    const uint64_t need = rel_sketch_ws_bytes();
+    if (plan->scratch_bytes < need) plan->scratch_bytes = need;
+    if (!ws || ws_bytes < plan->scratch_bytes) {
+      set_error("plan: sketching needs %llu workspace bytes",
+                (unsigned long long)plan->scratch_bytes);
+      return REL_E_CAPACITY;
+    }
+    rel_sketch_info info;
+    if ((r = rel_sketch(d, ws, ws_bytes, &info, st))) return r;
+    apply_sketch(info, gb_shape_width(m.shape), plan);
+  }
   return REL_OK;
 }
 
@@ -596,13 +721,88 @@ int64_t rel_profile_stop(int32_t* ids, float* ms, int64_t max) {
 
 const char* rel_kernel_name(int32_t id) {
   static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
-                                "join_build", "join_probe", "join_count"};
+                                "join_build", "join_probe", "join_count", "sketch", "gb_main_regs"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 
 uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs) {
   if (slots < 0 || n_aggs < 0) return 0;
   return gb_ws_bytes(slots, n_aggs);
+}
+
+uint64_t rel_sketch_ws_bytes(void) { return (sizeof(DevSketch) + 255) & ~(uint64_t)255; }
+
+rel_status rel_sketch(const rel_groupby_desc* d, void* ws, size_t ws_bytes, rel_sketch_info* out,
+                      void* stream) {
+  rel_status r = validate_desc(d);
+  if (r) return r;
+  if (!out) return set_error("sketch: NULL output"), REL_E_INVALID;
+  if (!ws || ws_bytes < rel_sketch_ws_bytes())
+    return set_error("sketch: workspace needs %llu bytes",
+                     (unsigned long long)rel_sketch_ws_bytes()),
+           REL_E_CAPACITY;
+  SketchParams sp;
+  std::memset(&sp, 0, sizeof sp);
+  sp.n_rows = d->n_rows;
+  for (int c = 0; c < d->n_cols; ++c) {
+    sp.col[c] = (const uint8_t*)d->cols[c].data;
+    sp.ctype[c] = d->cols[c].type;
+  }
+  sp.n_keys = d->n_keys;
+  sp.n_preds = d->n_preds;
+  int shift = 0, bits = 0;
+  for (int k = d->n_keys - 1; k >= 0; --k) {
+    const int w = elem_bits(d->cols[d->key_cols[k]].type);
+    sp.key_col[k] = d->key_cols[k];
+    sp.key_shift[k] = d->n_keys == 1 ? 0 : shift;
+    sp.key_mask[k] = w >= 64 ? ~0ull : ((1ull << w) - 1);
+    shift += w;
+    bits += w;
+  }
+  for (int i = 0; i < d->n_preds; ++i) {
+    sp.pred_col[i] = d->preds[i].col;
+    sp.pred_lo[i] = d->preds[i].lo;
+    sp.pred_hi[i] = d->preds[i].hi;
+  }
+  cudaStream_t st = as_stream(stream);
+  DevSketch* dev = (DevSketch*)ws;
+  if ((r = sketch_launch(sp, dev, st))) return r;
+  DevSketch h;
+  cudaError_t e = cudaMemcpyAsync(&h, dev, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the sketch");
+  std::memset(out, 0, sizeof *out);
+  out->n_rows = d->n_rows;
+  out->sample_rows = h.sample_rows;
+  out->kept = h.kept;
+  out->ndv = h.ndv;
+  out->singletons = h.singletons;
+  out->runs = h.runs;
+  out->key_bits = bits;
+  out->key_min = h.key_min;
+  out->key_max = h.key_max;
+  for (int i = 0; i < REL_SKETCH_TOP; ++i) {
+    out->top_key[i] = h.top_key[i];
+    out->top_count[i] = h.top_count[i];
+  }
+  for (int i = 0; i < 256; ++i) {
+    out->hll[i] = h.hll[i];
+    out->features[i] = (float)(h.hll[i] / 57.0);
+  }
+  const double kept = h.kept, ndv = h.ndv;
+  double top8 = 0;
+  for (int i = 0; i < 8; ++i) top8 += h.top_count[i];
+  float* f = out->features + 256;
+  f[0] = (float)std::log2(d->n_rows > 1 ? (double)d->n_rows : 1.0);
+  f[1] = (float)(h.kept ? ndv / kept : 0.0);
+  f[2] = (float)(h.kept ? std::log2((double)((uint64_t)h.key_max - (uint64_t)h.key_min) + 1.0)
+                        : 0.0);
+  f[3] = (float)(h.kept ? h.top_count[0] / kept : 0.0);
+  f[4] = (float)(h.kept ? top8 / kept : 0.0);
+  f[5] = (float)(h.ndv ? h.singletons / ndv : 0.0);
+  f[6] = (float)(h.runs ? kept / h.runs : 0.0);
+  f[7] = (float)(bits / 64.0);
+  return REL_OK;
 }
 
 uint64_t rel_join_ws_bytes(int64_t n_build) {
@@ -641,8 +841,8 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   if (!(ss == 0 || (ss >= 16 && ss <= SHARED_MAX_SLOTS && is_pow2((uint64_t)ss))))
     return set_error("group-by: smem_slots must be 0 or a power of two in [16, 4096]"),
            REL_E_INVALID;
-  if (!(ts == 0 || ts == 8 || ts == 16 || ts == 32))
-    return set_error("group-by: tiny_slots must be 0, 8, 16 or 32"), REL_E_INVALID;
+  if (!(ts == 0 || ts == 2 || ts == 4 || ts == 8 || ts == 16 || ts == 32))
+    return set_error("group-by: tiny_slots must be 0, 2, 4, 8, 16 or 32"), REL_E_INVALID;
   const uint64_t need = gb_ws_bytes(plan->slots, d->n_aggs);
   if (!ws || ws_bytes < need) {
     set_error("group-by: workspace needs %llu bytes", (unsigned long long)need);
@@ -679,10 +879,20 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   p.taggs = (unsigned long long*)(p.tkeys + plan->slots);
   p.log2_slots = log2_pow2((uint64_t)plan->slots);
   p.max_probe = (uint32_t)(plan->slots < 4096 ? plan->slots : 4096);
-  set_layers(p, plan);
+  if ((r = set_layers(p, plan, m.shape))) return r;
+  if (plan->tile_rows || plan->n_stages) {
+    const int32_t t = plan->tile_rows, ns = plan->n_stages;
+    if (t < 256 || t > 4096 || !is_pow2((uint64_t)t) || ns < 2 || ns > GB_MAX_STAGES)
+      return set_error("group-by: tile_rows must be a power of two in [256, 4096] and "
+                       "n_stages in [2, 8]"),
+             REL_E_INVALID;
+    p.req_tile = t;
+    p.req_stages = ns;
+  }
   cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
-  if ((r = run_main(p, m.shape, MODE_LAYERED, st))) return r;
+  const int mode = p.tiny_ns ? MODE_TINY : MODE_LAYERED;
+  if ((r = run_main(p, m.shape, mode, st))) return r;
   if ((r = gb_launch_compact(p, o, st))) return r;
   if (!n_groups_host) return REL_OK;
   HostHeader h;

@@ -274,9 +274,10 @@ __device__ __forceinline__ bool gtab_update_inl(const GbParams& p, uint64_t ek,
   return false;
 }
 
-// Out-of-line copy for the colder paths (values passed in registers).
+// Kept inline on every path: an out-of-line call taking the words by
+// reference makes the compiler keep them in local memory on every row.
 template <class S>
-__device__ __noinline__ bool gtab_update(const GbParams& p, uint64_t ek, const Vals<S::A>& x) {
+__device__ __forceinline__ bool gtab_update(const GbParams& p, uint64_t ek, const Vals<S::A>& x) {
   return gtab_update_inl<S>(p, ek, x);
 }
 
@@ -303,7 +304,6 @@ __device__ __noinline__ bool gset_insert(const GbParams& p, uint64_t ek) {
 
 // ---------------------------------------------------------------- backends
 
-constexpr uint32_t TINY_MULT = 0x9E3779B1u;
 constexpr uint32_t SHARED_MULT = 0x85EBCA77u;
 
 // Thread-private -> CTA-shared -> global, each layer optional.  Only the
@@ -317,9 +317,11 @@ struct BeLayered {
   uint64_t* tres;            // [tiny_slots][A] reduced words (flush)
   uint64_t* sk;              // [smem_slots] stored keys
   unsigned long long* sacc;  // [smem_slots][A]
+  unsigned int* seen_all;    // thread-private slots any row of this CTA used
+  uint32_t seen;             // ... by this thread (pinned slots may stay unused)
 
   __host__ __device__ static uint64_t bytes(uint32_t tiny, uint32_t shared) {
-    return 8ull * tiny * (1 + (uint64_t)A * GB_BLOCK + A) + 8ull * shared * (1 + A);
+    return 8ull * tiny * (1 + (uint64_t)A * GB_BLOCK + A) + 8ull * shared * (1 + A) + 8ull;
   }
   __device__ void bind(uint8_t* area, const GbParams& p) {
     tk = (uint64_t*)area;
@@ -327,12 +329,16 @@ struct BeLayered {
     tres = tacc + (size_t)p.tiny_slots * A * GB_BLOCK;
     sk = tres + (size_t)p.tiny_slots * A;
     sacc = (unsigned long long*)(sk + p.smem_slots);
+    seen_all = (unsigned int*)(sacc + (size_t)p.smem_slots * A);
   }
   __device__ void init(const GbParams& p) {
     const uint32_t n1 = p.tiny_slots * (1 + A * GB_BLOCK);
-    for (uint32_t i = threadIdx.x; i < n1; i += GB_BLOCK) tk[i] = 0;
+    for (uint32_t i = threadIdx.x; i < n1; i += GB_BLOCK)
+      tk[i] = (p.tiny_frozen && i < p.tiny_slots) ? p.tiny_init[i] : 0;
     const uint32_t n2 = p.smem_slots * (1 + A);
     for (uint32_t i = threadIdx.x; i < n2; i += GB_BLOCK) sk[i] = 0;
+    seen = 0;
+    if (threadIdx.x == 0) *seen_all = 0;
   }
   __device__ __forceinline__ void tiny_rmw(const GbParams& p, uint32_t s, const Vals<A>& x) {
     uint64_t* w = tacc + (size_t)s * A * GB_BLOCK + threadIdx.x;
@@ -350,9 +356,13 @@ struct BeLayered {
   __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>& x) {
     int where = 0;  // 1: thread-private slot s, 2: CTA-shared slot s, 0: neither
     uint32_t s = 0;
-    if (p.tiny_slots) {
+    if (p.tiny_slots && p.tiny_frozen) {
+      // pinned keys, each at its own hash slot: one probe decides
+      s = small_slot_of(ek, p.tiny_slots - 1, p.tiny_mult);
+      if (tk[s] == ek) where = 1;
+    } else if (p.tiny_slots) {
       const uint32_t mask = p.tiny_slots - 1;
-      s = small_slot_of(ek, mask, TINY_MULT);
+      s = small_slot_of(ek, mask, p.tiny_mult);
 #pragma unroll 1
       for (uint32_t i = 0; i < p.tiny_probes; ++i) {
         uint64_t k = *(volatile uint64_t*)(tk + s);
@@ -385,6 +395,7 @@ struct BeLayered {
       }
     }
     if (where == 1) {
+      seen |= 1u << s;
       tiny_rmw(p, s, x);
       return true;
     }
@@ -396,8 +407,10 @@ struct BeLayered {
     return gtab_update_inl<S>(p, ek, x);
   }
   __device__ void flush(const GbParams& p) {
-    named_sync(GB_BLOCK);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ws = __reduce_or_sync(0xffffffffu, seen);
+    if (lane == 0 && ws) atomicOr(seen_all, ws);
+    named_sync(GB_BLOCK);
     if (p.tiny_slots) {
       for (uint32_t pr = warp; pr < p.tiny_slots * A; pr += GB_BLOCK / 32) {
         const uint32_t s = pr / A, a = pr % A;
@@ -417,7 +430,8 @@ struct BeLayered {
         if (lane == 0) tres[s * A + a] = v;
       }
       named_sync(GB_BLOCK);
-      if (threadIdx.x < p.tiny_slots && tk[threadIdx.x] != 0) {
+      if (threadIdx.x < p.tiny_slots && tk[threadIdx.x] != 0 &&
+          ((*seen_all >> threadIdx.x) & 1u)) {
         Vals<A> x;
 #pragma unroll
         for (int a = 0; a < A; ++a) x.v[a] = tres[threadIdx.x * A + a];
@@ -431,6 +445,101 @@ struct BeLayered {
 #pragma unroll
       for (int a = 0; a < A; ++a) x.v[a] = sacc[(size_t)s * A + a];
       gtab_update<S>(p, k, x);
+    }
+  }
+};
+
+// Pinned keys held in registers: each thread keeps NS x A accumulator words
+// in registers and updates the row's group with unrolled, predicated adds and
+// maxes -- independent ALU work with no shared-memory dependency chain.  The
+// row's key is checked against the pinned table (perfect hash, one probe)
+// and mapped to a dense id in [0, NS); a key the plan did not pin goes to the
+// global table.  At the end each warp reduces its lanes with shuffles and the
+// CTA merges the per-warp partials into the global table.
+template <class S, int NS>
+struct BeRegs {
+  using Shape = S;
+  static constexpr int A = S::A;
+  static constexpr int ID = relhost::K_GB_REGS;
+  uint64_t acc[NS][A];
+  uint32_t seen;            // bit j: this thread updated dense slot j
+  uint64_t* tk;             // [tiny_slots] pinned stored keys
+  uint64_t* part;           // [GB_BLOCK / 32][NS][A] per-warp partials (flush)
+  unsigned int* seen_all;   // OR of every thread's seen bits
+
+  __host__ __device__ static uint64_t bytes(uint32_t tiny, uint32_t) {
+    return 8ull * tiny + 8ull * (GB_BLOCK / 32) * NS * A + 8ull;
+  }
+  __device__ void bind(uint8_t* area, const GbParams& p) {
+    tk = (uint64_t*)area;
+    part = tk + p.tiny_slots;
+    seen_all = (unsigned int*)(part + (GB_BLOCK / 32) * NS * A);
+  }
+  __device__ void init(const GbParams& p) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+#pragma unroll
+      for (int a = 0; a < A; ++a) acc[j][a] = 0;
+    seen = 0;
+    for (uint32_t i = threadIdx.x; i < p.tiny_slots; i += GB_BLOCK) tk[i] = p.tiny_init[i];
+    if (threadIdx.x == 0) *seen_all = 0;
+  }
+  __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>& x) {
+    const uint32_t s = small_slot_of(ek, p.tiny_slots - 1, p.tiny_mult);
+    if (tk[s] != ek) return gtab_update<S>(p, ek, x);
+    const uint32_t d = (uint32_t)(p.tiny_dense >> (4u * s)) & 15u;
+    seen |= 1u << d;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const bool hit = d == (uint32_t)j;
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        if (!live_agg<S>(p, a)) continue;
+        const uint64_t o = acc[j][a];
+        if (is_umax<S>(p, a))
+          acc[j][a] = (hit && x.v[a] > o) ? x.v[a] : o;
+        else
+          acc[j][a] = o + (hit ? x.v[a] : 0ull);
+      }
+    }
+    return true;
+  }
+  __device__ void flush(const GbParams& p) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const bool um = is_umax<S>(p, a);
+        uint64_t v = acc[j][a];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, v, o);
+          v = um ? (v > y ? v : y) : v + y;
+        }
+        if (lane == 0) part[(warp * NS + j) * A + a] = v;
+      }
+    }
+    const uint32_t ws = __reduce_or_sync(0xffffffffu, seen);
+    if (lane == 0 && ws) atomicOr(seen_all, ws);
+    named_sync(GB_BLOCK);
+    // thread j merges dense slot j: its key is the pinned key with dense id j
+    for (uint32_t s = threadIdx.x; s < p.tiny_slots; s += GB_BLOCK) {
+      if (tk[s] == 0) continue;
+      const int j = (int)((p.tiny_dense >> (4u * s)) & 15u);
+      if (j >= NS || !((*seen_all >> j) & 1u)) continue;  // no row of this key here
+      Vals<A> x;
+#pragma unroll
+      for (int a = 0; a < A; ++a) {
+        const bool um = is_umax<S>(p, a);
+        uint64_t v = 0;
+        for (int w = 0; w < GB_BLOCK / 32; ++w) {
+          const uint64_t y = part[(w * NS + j) * A + a];
+          v = um ? (v > y ? v : y) : v + y;
+        }
+        x.v[a] = v;
+      }
+      gtab_update<S>(p, tk[s], x);
     }
   }
 };
@@ -497,9 +606,9 @@ template <class S, class BE, bool KEYSET, bool USE_TMA>
 __global__ void __launch_bounds__(GB_THREADS) gb_main(const __grid_constant__ GbParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* full = (uint64_t*)smem;        // [n_stages]
-  uint64_t* empty = (uint64_t*)smem + 8;   // [n_stages]
-  int* abort_flag = (int*)(smem + 120);
-  uint8_t* area = smem + 128;
+  uint64_t* empty = (uint64_t*)smem + GB_MAX_STAGES;  // [n_stages]
+  int* abort_flag = (int*)(smem + 16 * GB_MAX_STAGES);
+  uint8_t* area = smem + GB_SMEM_HEAD;
   BE be;
   be.bind(area, p);
   const bool consumer = threadIdx.x < GB_BLOCK;
@@ -655,10 +764,26 @@ auto with_keyset_shape(int shape, F&& f) {
   }
 }
 
+// Register-privatised kernels: shapes of at most 5 words, 4 or 8 dense slots.
+template <class F>
+auto with_regs(int shape, uint32_t ns, F&& f) {
+  auto pick = [&](auto s) {
+    using S = decltype(s);
+    return ns <= 4 ? f(BeRegs<S, 4>{}) : f(BeRegs<S, 8>{});
+  };
+  switch (shape) {
+    case SHAPE_Q1: return pick(ShapeQ1{});
+    case SHAPE_KV4_32: return pick(ShapeKV<int32_t, 4>{});
+    case SHAPE_KV2_64: return pick(ShapeKV<int64_t, 2>{});
+    case SHAPE_KV2_32: return pick(ShapeKV<int32_t, 2>{});
+    default: return pick(ShapeKV<int64_t, 4>{});
+  }
+}
+
 template <class S, class BE, bool KEYSET, bool TMA>
 size_t smem_of(const GbParams& p) {
   const uint64_t be = (BE::bytes(p.tiny_slots, p.smem_slots) + 127) & ~127ull;
-  return 128 + be + (TMA ? (size_t)p.n_stages * p.stage_bytes : 0);
+  return GB_SMEM_HEAD + be + (TMA ? (size_t)p.n_stages * p.stage_bytes : 0);
 }
 
 template <class S, class BE, bool KEYSET, bool TMA>
@@ -703,6 +828,8 @@ int gb_shape_width(int shape) {
 
 uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t tiny_slots, uint32_t smem_slots) {
   if (mode == MODE_KEYSET) return 8ull * smem_slots;
+  if (mode == MODE_TINY)
+    return with_regs(shape, 8, [&](auto be) { return decltype(be)::bytes(tiny_slots, smem_slots); });
   return with_shape(shape, [&](auto s) {
     return BeLayered<decltype(s)>::bytes(tiny_slots, smem_slots);
   });
@@ -714,6 +841,12 @@ int gb_ctas_per_sm(const GbParams& p, int shape, int mode, bool tma) {
       using S = decltype(s);
       return tma ? occupancy<S, BeKeySet<S>, true, true>(p)
                  : occupancy<S, BeKeySet<S>, true, false>(p);
+    });
+  if (mode == MODE_TINY)
+    return with_regs(shape, p.tiny_ns, [&](auto be) {
+      using BE = decltype(be);
+      using S = typename BE::Shape;
+      return tma ? occupancy<S, BE, false, true>(p) : occupancy<S, BE, false, false>(p);
     });
   return with_shape(shape, [&](auto s) {
     using S = decltype(s);
@@ -729,6 +862,12 @@ rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool tma, cuda
       using S = decltype(s);
       return tma ? launch_one<S, BeKeySet<S>, true, true>(p, st)
                  : launch_one<S, BeKeySet<S>, true, false>(p, st);
+    });
+  if (mode == MODE_TINY)
+    return with_regs(shape, p.tiny_ns, [&](auto be) {
+      using BE = decltype(be);
+      using S = typename BE::Shape;
+      return tma ? launch_one<S, BE, false, true>(p, st) : launch_one<S, BE, false, false>(p, st);
     });
   return with_shape(shape, [&](auto s) {
     using S = decltype(s);

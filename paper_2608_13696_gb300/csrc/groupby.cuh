@@ -8,11 +8,12 @@ namespace rel {
 
 constexpr int GB_BLOCK = 256;                // consumer threads per CTA
 constexpr int GB_THREADS = GB_BLOCK + 32;    // + one TMA producer warp
-constexpr int GB_MAX_STAGES = 4;
+constexpr int GB_MAX_STAGES = 8;
+constexpr int GB_SMEM_HEAD = 256;  // full[8] and empty[8] mbarriers, abort flag
 constexpr int TINY_MAX_SLOTS = 32;
 constexpr int SHARED_MAX_SLOTS = 4096;
 
-enum GbMode : int { MODE_LAYERED = 0, MODE_KEYSET = 1 };
+enum GbMode : int { MODE_LAYERED = 0, MODE_KEYSET = 1, MODE_TINY = 2 };
 
 // Row shapes.  The specialised ones fix column types and aggregate kinds at
 // compile time; KV4 / KV2 hold their aggregates in the internal order
@@ -55,6 +56,12 @@ struct GbParams {
   uint32_t tiny_probes;    // probes in the thread-private table before moving on
   uint32_t smem_slots;     // 0 or a power of two <= SHARED_MAX_SLOTS (CTA-shared table)
   uint32_t shared_probes;  // probes in the CTA-shared table before moving on
+  uint32_t tiny_mult;      // multiplier of the thread-private slot hash
+  uint32_t tiny_frozen;    // 1: slots preloaded from tiny_init, no other key admitted
+  uint64_t tiny_init[TINY_MAX_SLOTS];  // stored keys per slot (0 = empty)
+  uint64_t tiny_dense;     // register mode: 4-bit dense id of each of <= 16 slots
+  uint32_t tiny_ns;        // register mode: dense slots compiled in (4 or 8)
+  int32_t req_tile, req_stages;  // staging chosen by the plan (0: automatic)
   // global table (or key set in MODE_KEYSET)
   uint64_t* tkeys;
   unsigned long long* taggs;  // slots x n_aggs words

@@ -140,6 +140,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Shared-memory access by 32-bit shared-window address (ordered with every
+// other memory access of the thread).
+__device__ __forceinline__ uint64_t lds64(uint32_t a) {
+  uint64_t v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts64(uint32_t a, uint64_t v) {
+  asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
 // Barrier among the first `count` threads of the CTA (named barrier 1).
 __device__ __forceinline__ void named_sync(uint32_t count) {
   asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
@@ -179,7 +190,9 @@ enum KernelId : int {
   K_JOIN_BUILD = 3,
   K_JOIN_PROBE = 4,
   K_JOIN_COUNT = 5,
-  K_COUNT_IDS = 6
+  K_SKETCH = 6,
+  K_GB_REGS = 7,
+  K_COUNT_IDS = 8
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "REL_OK", -1: "REL_E_INVALID", -2: "REL_E_CAPACITY", -3: "REL
 U8, I32, I64 = 0, 1, 2
 OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
 VAR_AUTO, VAR_SMEM, VAR_GLOBAL, VAR_PARTITIONED = 0, 1, 2, 3
-PLAN_EXACT, PLAN_LEARNED, PLAN_GENERIC = 1, 2, 4
+PLAN_EXACT, PLAN_LEARNED, PLAN_GENERIC, PLAN_SKETCH = 1, 2, 4, 8
 OP_GROUPBY, OP_JOIN_PROBE = 0, 1
 MAX_COLS, MAX_KEYS, MAX_PREDS, MAX_AGGS = 8, 4, 4, 8
 
@@ -68,19 +68,35 @@ class Plan(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int64), ("variant", ctypes.c_int32),
                 ("smem_slots", ctypes.c_int32), ("workspace_bytes", ctypes.c_uint64),
                 ("scratch_bytes", ctypes.c_uint64), ("est_groups", ctypes.c_int64),
-                ("flags", ctypes.c_uint32), ("tiny_slots", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("tiny_slots", ctypes.c_int32),
+                ("tiny_mult", ctypes.c_uint32), ("n_hot", ctypes.c_int32),
+                ("hot_keys", ctypes.c_int64 * 32), ("tile_rows", ctypes.c_int32),
+                ("n_stages", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"Plan(slots={self.slots}, variant={self.variant}, tiny_slots={self.tiny_slots}, "
+                f"n_hot={self.n_hot}, "
                 f"smem_slots={self.smem_slots}, workspace_bytes={self.workspace_bytes}, "
                 f"est_groups={self.est_groups})")
 
     def layers(self, tiny: int, smem: int, variant: int | None = None) -> "Plan":
-        """Set the per-CTA layers (thread-private slots, CTA-shared slots)."""
+        """Set the per-CTA layers (thread-private slots, CTA-shared slots); drops
+        any pinned hot keys."""
         self.tiny_slots, self.smem_slots = tiny, smem
+        self.n_hot = 0
         if variant is not None:
             self.variant = variant
         return self
+
+
+class SketchInfo(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("sample_rows", ctypes.c_int32),
+                ("kept", ctypes.c_int32), ("ndv", ctypes.c_int32),
+                ("singletons", ctypes.c_int32), ("runs", ctypes.c_int32),
+                ("key_bits", ctypes.c_int32), ("key_min", ctypes.c_int64),
+                ("key_max", ctypes.c_int64), ("top_key", ctypes.c_int64 * 32),
+                ("top_count", ctypes.c_int32 * 32), ("hll", ctypes.c_uint8 * 256),
+                ("features", ctypes.c_float * 264)]
 
 
 class JoinTableC(ctypes.Structure):
@@ -101,7 +117,8 @@ _lib = None
 EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join_ws_bytes",
            "rel_join_build", "rel_join_probe", "rel_last_error", "rel_launch_count",
            "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name",
-           "rel_groupby_agg_static"]
+           "rel_groupby_agg_static", "rel_sketch", "rel_sketch_ws_bytes"]
+SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
 
 
@@ -149,6 +166,11 @@ def load(build_if_stale: bool = True):
         L.rel_profile_stop.argtypes = [vp, vp, i64]
         L.rel_kernel_name.restype = ctypes.c_char_p
         L.rel_kernel_name.argtypes = [i32]
+        L.rel_sketch_ws_bytes.restype = u64
+        L.rel_sketch_ws_bytes.argtypes = []
+        L.rel_sketch.restype = i32
+        L.rel_sketch.argtypes = [ctypes.POINTER(GroupByDesc), vp, ctypes.c_size_t,
+                                 ctypes.POINTER(SketchInfo), vp]
         L.rel_groupby_agg_static.restype = i32
         L.rel_groupby_agg_static.argtypes = [ctypes.POINTER(GroupByDesc), i64, vp,
                                              ctypes.POINTER(ctypes.c_void_p), i64,
@@ -285,6 +307,17 @@ def groupby_static(q: dict, max_groups: int, capacity: int | None = None, stream
                                     ctypes.byref(n), _stream(stream)))
     g = n.value
     return keys[:g], [a[:g] for a in aggs]
+
+
+def sketch(q: dict, stream=None) -> "SketchInfo":
+    """rel_sketch: the 4096-row sample summary of a group-by input."""
+    L = load()
+    d = _Desc(q)
+    ws = _ws(L.rel_sketch_ws_bytes(), q["cols"][0].device)
+    out = SketchInfo()
+    _check(L.rel_sketch(ctypes.byref(d.d), ws.data_ptr(), ws.numel(), ctypes.byref(out),
+                        _stream(stream)))
+    return out
 
 
 class JoinTable:

@@ -1,0 +1,91 @@
+"""GPU parity of the sample sketch (rel_sketch) against the oracle's sketch --
+integer fields bit-exact, features to float32 rounding -- and of group-bys
+planned from it (hot keys pinned in thread-private slots) against the oracle
+group-by."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2608_13696_gb300 import rel
+
+from gpu_util import canon_groupby, query_to_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def cases():
+    li = synth.lineitem(250_000, seed=3)
+    zk, zv = synth.zipf_kv(500_000, seed=4, n_ranks=100_000)
+    fk, fv = synth.few_keys_kv(300_000, n_keys=4, seed=5)
+    k32 = synth.uniform(50_000, -7, 7, seed=6, tag=3, dtype=np.int32)
+    runs = np.repeat(np.arange(127, dtype=np.int64), 64)
+    sent = np.array([np.iinfo(np.int64).min] * 10 + list(range(90)), dtype=np.int64)
+    return {
+        "lineitem": oracle.lineitem_query(li),
+        "zipf": oracle.kv_query(zk, zv),
+        "four": oracle.kv_query(fk, fv),
+        "int32": oracle.kv_query(k32, zv[:50_000]),
+        "runs": oracle.kv_query(runs, runs),
+        "tiny_n": oracle.kv_query(zk[:37], zv[:37]),
+        "sentinel": oracle.kv_query(sent, sent),
+        "filtered_out": oracle.lineitem_query(synth.lineitem(9000, seed=7), date_hi=-1),
+    }
+
+
+CASES = cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sketch_matches_oracle(name):
+    q = CASES[name]
+    s = rel.sketch(query_to_cuda(q))
+    e = oracle.sketch(q)
+    for f in ("sample_rows", "kept", "ndv", "singletons", "runs", "key_min", "key_max",
+              "key_bits"):
+        assert getattr(s, f) == e[f], f
+    assert list(s.top_key) == e["top_key"].tolist()
+    assert list(s.top_count) == e["top_count"].tolist()
+    assert bytes(s.hll) == e["hll"].tobytes()
+    np.testing.assert_allclose(np.array(s.features, dtype=np.float64), e["features"],
+                               rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("name", ["lineitem", "zipf", "four", "int32", "sentinel", "runs"])
+@pytest.mark.parametrize("flags", [rel.PLAN_EXACT | rel.PLAN_SKETCH, rel.PLAN_SKETCH])
+def test_sketch_planned_groupby(name, flags):
+    q = CASES[name]
+    qc = query_to_cuda(q)
+    if flags == rel.PLAN_SKETCH:
+        plan = rel.plan_groupby(qc, flags=flags, groups_hint=len(np.unique(q["cols"][0])))
+    else:
+        plan = rel.plan_groupby(qc, flags=flags)
+    k, a = rel.groupby(qc, plan=plan)
+    torch.cuda.synchronize()
+    gk, ga = canon_groupby(k, a)
+    ek, ea = oracle.groupby(q)
+    np.testing.assert_array_equal(gk, ek)
+    np.testing.assert_array_equal(ga, ea)
+
+
+def test_pinned_keys_are_the_heavy_hitters():
+    q = CASES["four"]
+    plan = rel.plan_groupby(query_to_cuda(q), flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
+    assert plan.n_hot == 4 and plan.tiny_slots == 4  # the fewest collision-free slots
+    assert sorted(plan.hot_keys[:4]) == sorted(synth.mix64_signed(i) for i in (1, 2, 3, 4))
+    qz = CASES["zipf"]
+    plan = rel.plan_groupby(query_to_cuda(qz), flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
+    assert plan.n_hot >= 1 and plan.hot_keys[0] == synth.mix64_signed(1)
+    assert plan.smem_slots > 0  # warm keys still have a CTA-shared layer
+
+
+def test_bad_hot_keys_rejected():
+    q = CASES["four"]
+    qc = query_to_cuda(q)
+    plan = rel.plan_groupby(qc, flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
+    plan.n_hot = 2
+    plan.hot_keys[1] = plan.hot_keys[0]  # two keys on one slot
+    with pytest.raises(rel.RelError) as e:
+        rel.groupby(qc, plan=plan)
+    assert e.value.status == rel.REL_E_INVALID
