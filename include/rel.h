@@ -60,7 +60,8 @@ typedef int32_t rel_status;
 #define REL_VAR_AUTO 0        /* let rel_plan_size choose                       */
 #define REL_VAR_SMEM 1        /* per-CTA shared-memory tables, merged at the end */
 #define REL_VAR_GLOBAL 2      /* one global open-addressing table               */
-#define REL_VAR_PARTITIONED 3 /* reserved: radix partition, then per-part agg   */
+#define REL_VAR_PARTITIONED 3 /* hash-partition the rows, then one shared-memory
+                                 table per partition (key + int64 value inputs)  */
 
 /* limits of one group-by descriptor */
 #define REL_MAX_COLS 8
@@ -140,6 +141,9 @@ typedef struct {
   int64_t hot_keys[REL_MAX_HOT];
   int32_t tile_rows;        /* rows per staged tile (256..2048, power of two); 0 = auto */
   int32_t n_stages;         /* staging ring depth (2..8); 0 = auto                    */
+  int32_t part_bits;        /* REL_VAR_PARTITIONED: log2 of the partition count
+                               (4..13); smem_slots is then each partition's table */
+  int32_t reserved;
 } rel_plan;
 
 #define REL_OP_GROUPBY 0
@@ -185,6 +189,11 @@ rel_status rel_groupby_agg(const rel_groupby_desc* desc, const rel_plan* plan, v
 /* Device bytes rel_groupby_agg needs for `slots` table slots and `n_aggs`
  * aggregates. */
 uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs);
+
+/* Device bytes rel_groupby_agg needs for a (possibly edited) plan over
+ * n_rows rows with n_aggs aggregates -- the partitioned variant also keeps a
+ * 16-byte record per row. */
+uint64_t rel_plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows);
 
 /* ------------------------------------------------------ sample sketch */
 

@@ -403,6 +403,91 @@ uint64_t gb_ws_bytes(int64_t slots, int32_t n_aggs) {
   return HEADER_BYTES + (uint64_t)slots * 8ull * (1ull + (uint64_t)n_aggs);
 }
 
+// ------------------------------------------------- partitioned variant (P)
+
+constexpr uint32_t PART_MAX_GRID = 512;  // CTAs of the histogram / scatter passes
+
+bool part_shape(int shape) {
+  return shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 || shape == SHAPE_KV2_64 ||
+         shape == SHAPE_KV2_32;
+}
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Workspace after the header and spill table: histogram, partition starts,
+// records.
+struct PartLayout {
+  uint64_t hist, starts, recs, end;
+};
+
+PartLayout part_layout(int64_t slots, int32_t n_aggs, int bits, int64_t n_rows) {
+  PartLayout L;
+  const uint64_t P = 1ull << bits;
+  L.hist = align_up(gb_ws_bytes(slots, n_aggs), 256);
+  L.starts = align_up(L.hist + 4ull * P * PART_MAX_GRID, 256);
+  L.recs = align_up(L.starts + 8ull * (P + 1), 256);
+  L.end = L.recs + sizeof(PartRec) * (uint64_t)(n_rows > 0 ? n_rows : 1);
+  return L;
+}
+
+uint64_t plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows) {
+  if (plan->variant == REL_VAR_PARTITIONED)
+    return part_layout(plan->slots, n_aggs, plan->part_bits, n_rows).end;
+  return gb_ws_bytes(plan->slots, n_aggs);
+}
+
+// Histogram, scan, scatter, per-partition aggregation.  The histogram and
+// scatter passes must see every row on the same CTA and classify it the same
+// way, so both run with one grid size, one tile size and one pinned set.
+rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const GbOut& o,
+                           void* ws, cudaStream_t st) {
+  const PartLayout L = part_layout(plan->slots, p.n_aggs, plan->part_bits, p.n_rows);
+  uint8_t* base = (uint8_t*)ws;
+  p.part_bits = (uint32_t)plan->part_bits;
+  p.hist = (uint32_t*)(base + L.hist);
+  p.part_start = (unsigned long long*)(base + L.starts);
+  p.recs = (PartRec*)(base + L.recs);
+  uint32_t grid = 2u * (uint32_t)relhost::device_sms();
+  p.fixed_grid = grid > PART_MAX_GRID ? PART_MAX_GRID : grid;
+  const uint32_t agg_slots = p.smem_slots;
+  p.smem_slots = 0;  // passes 1-2 keep only the pinned thread-private layer
+  if (!p.tiny_frozen) {
+    p.tiny_slots = 0;
+    p.tiny_probes = 0;
+  }
+  const bool tma = tma_ok(p);
+  if (!configure_stages(p, shape, MODE_PSCATTER, tma))
+    return set_error("group-by: partition scatter does not fit"), REL_E_UNSUPPORTED;
+  const int T = p.tile_rows, NS = p.n_stages;
+  p.req_tile = T;
+  p.req_stages = NS;
+  if (!configure_stages(p, shape, MODE_PHIST, tma) || p.tile_rows != T)
+    return set_error("group-by: partition histogram does not fit"), REL_E_UNSUPPORTED;
+  rel_status r;
+  if ((r = gb_launch_main(p, shape, MODE_PHIST, tma, st))) return r;
+  if ((r = gb_launch_part_scan(p, st))) return r;
+  set_stages(p, T, NS);
+  if ((r = gb_launch_main(p, shape, MODE_PSCATTER, tma, st))) return r;
+  p.smem_slots = agg_slots;
+  return gb_launch_part_agg(p, shape, o, st);
+}
+
+// Many groups over key + value rows: partition instead of one big table.
+void choose_partitioned(int64_t est, int64_t n_rows, rel_plan* plan) {
+  uint64_t per = (uint64_t)(est / 768);
+  int bits = 4;
+  while (bits < PART_MAX_BITS && (1ull << bits) < per) ++bits;
+  plan->variant = REL_VAR_PARTITIONED;
+  plan->part_bits = bits;
+  // each partition's table at load <= 0.4 on average
+  const uint64_t keys_per_part = (uint64_t)est >> bits;
+  plan->smem_slots = (int32_t)next_pow2(keys_per_part * 5 / 2 < 256 ? 256 : keys_per_part * 5 / 2);
+  if (plan->smem_slots > SHARED_MAX_SLOTS) plan->smem_slots = SHARED_MAX_SLOTS;
+  plan->tiny_slots = 0;     // pinned heavy hitters only (from a sketch)
+  plan->slots = (int64_t)next_pow2((uint64_t)(est / 4 > 65536 ? est / 4 : 65536));
+  (void)n_rows;
+}
+
 // Per-CTA layers for an expected number of groups.
 void choose_layers(int64_t est, int words, rel_plan* plan) {
   plan->tiny_slots = 0;
@@ -618,7 +703,9 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
   plan->est_groups = est;
   plan->slots = (int64_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
   choose_layers(est, gb_shape_width(m.shape), plan);
-  plan->workspace_bytes = gb_ws_bytes(plan->slots, d->n_aggs);
+  if (plan->variant == REL_VAR_GLOBAL && part_shape(m.shape) && d->n_rows < (1ll << 32))
+    choose_partitioned(est, d->n_rows, plan);
+  plan->workspace_bytes = plan_ws_bytes(plan, d->n_aggs, d->n_rows);
   if ((flags & REL_PLAN_SKETCH) && d->n_rows > 0) {
     const uint64_t need = rel_sketch_ws_bytes();
     if (plan->scratch_bytes < need) plan->scratch_bytes = need;
@@ -721,13 +808,23 @@ int64_t rel_profile_stop(int32_t* ids, float* ms, int64_t max) {
 
 const char* rel_kernel_name(int32_t id) {
   static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
-                                "join_build", "join_probe", "join_count", "sketch", "gb_main_regs"};
+                                "join_build", "join_probe", "join_count", "sketch", "gb_main_regs",
+                                "gb_part_hist", "gb_part_scan", "gb_part_scatter",
+                                "gb_part_agg"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 
 uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs) {
   if (slots < 0 || n_aggs < 0) return 0;
   return gb_ws_bytes(slots, n_aggs);
+}
+
+uint64_t rel_plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows) {
+  if (!plan || n_aggs < 0 || n_rows < 0 || plan->slots < 0) return 0;
+  if (plan->variant == REL_VAR_PARTITIONED &&
+      (plan->part_bits < 0 || plan->part_bits > PART_MAX_BITS))
+    return 0;
+  return plan_ws_bytes(plan, n_aggs, n_rows);
 }
 
 uint64_t rel_sketch_ws_bytes(void) { return (sizeof(DevSketch) + 255) & ~(uint64_t)255; }
@@ -843,7 +940,18 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
            REL_E_INVALID;
   if (!(ts == 0 || ts == 2 || ts == 4 || ts == 8 || ts == 16 || ts == 32))
     return set_error("group-by: tiny_slots must be 0, 2, 4, 8, 16 or 32"), REL_E_INVALID;
-  const uint64_t need = gb_ws_bytes(plan->slots, d->n_aggs);
+  const uint64_t need = gb_ws_bytes(plan->slots, d->n_aggs);  // zeroed part
+  if (plan->variant == REL_VAR_PARTITIONED &&
+      (plan->part_bits < 4 || plan->part_bits > PART_MAX_BITS || plan->smem_slots < 256 ||
+       plan->smem_slots > SHARED_MAX_SLOTS || d->n_rows >= (1ll << 32)))
+    return set_error("group-by: partitioned plans need part_bits in [4, 13], smem_slots in "
+                     "[256, 4096] and fewer than 2^32 rows"),
+           REL_E_INVALID;
+  const uint64_t need_all = plan_ws_bytes(plan, d->n_aggs, d->n_rows);
+  if (!ws || ws_bytes < need_all) {
+    set_error("group-by: workspace needs %llu bytes", (unsigned long long)need_all);
+    return REL_E_CAPACITY;
+  }
   if (!ws || ws_bytes < need) {
     set_error("group-by: workspace needs %llu bytes", (unsigned long long)need);
     return REL_E_CAPACITY;
@@ -891,8 +999,12 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   }
   cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
-  const int mode = p.tiny_ns ? MODE_TINY : MODE_LAYERED;
-  if ((r = run_main(p, m.shape, mode, st))) return r;
+  if (plan->variant == REL_VAR_PARTITIONED && part_shape(m.shape)) {
+    if ((r = run_partitioned(p, plan, m.shape, o, ws, st))) return r;
+  } else {
+    const int mode = p.tiny_ns ? MODE_TINY : MODE_LAYERED;
+    if ((r = run_main(p, m.shape, mode, st))) return r;
+  }
   if ((r = gb_launch_compact(p, o, st))) return r;
   if (!n_groups_host) return REL_OK;
   HostHeader h;

@@ -210,13 +210,17 @@ struct ShapeKV {
     const int64_t key = (int64_t)q.k[r];
     const uint64_t val = (uint64_t)q.v[r];
     ek = (uint64_t)key ^ KEY_FLIP;
+    from_val(val, x);
+    return true;
+  }
+  // the aggregate words of a row with value val
+  __device__ __forceinline__ static void from_val(uint64_t val, Vals<A>& x) {
     x.v[0] = val;
     x.v[1] = 1;
     if constexpr (NA == 4) {
       x.v[2] = val ^ MIN_FLIP;
       x.v[3] = val ^ MAX_FLIP;
     }
-    return true;
   }
 };
 
@@ -312,6 +316,7 @@ template <class S>
 struct BeLayered {
   static constexpr int A = S::A;
   static constexpr int ID = relhost::K_GB_LAYERED;
+  static constexpr int SIDE = SIDE_AGG;
   uint64_t* tk;              // [tiny_slots] stored keys
   uint64_t* tacc;            // [tiny_slots][A][GB_BLOCK] thread-private words
   uint64_t* tres;            // [tiny_slots][A] reduced words (flush)
@@ -461,6 +466,7 @@ struct BeRegs {
   using Shape = S;
   static constexpr int A = S::A;
   static constexpr int ID = relhost::K_GB_REGS;
+  static constexpr int SIDE = SIDE_AGG;
   uint64_t acc[NS][A];
   uint32_t seen;            // bit j: this thread updated dense slot j
   uint64_t* tk;             // [tiny_slots] pinned stored keys
@@ -544,11 +550,102 @@ struct BeRegs {
   }
 };
 
+// ------------------------------------------------- partitioned variant (P)
+
+// Partition of a stored key: top bits of a multiplicative hash independent
+// of the table hashes.
+__device__ __forceinline__ uint32_t part_of(uint64_t ek, uint32_t bits) {
+  return (uint32_t)((ek * 0xD6E8FEB86659FD93ull) >> (64 - bits));
+}
+
+__device__ __forceinline__ bool is_pinned(const GbParams& p, const uint64_t* tk, uint64_t ek) {
+  if (!p.tiny_frozen) return false;
+  return tk[small_slot_of(ek, p.tiny_slots - 1, p.tiny_mult)] == ek;
+}
+
+// Pass 1: rows per (partition, CTA), pinned keys excluded.
+template <class S>
+struct BePartHist {
+  static constexpr int A = S::A;
+  static constexpr int ID = relhost::K_GB_PHIST;
+  static constexpr int SIDE = SIDE_SKIP;
+  uint64_t* tk;
+  unsigned int* cnt;
+  __host__ __device__ static uint64_t bytes(uint32_t tiny, uint32_t) {
+    return 8ull * tiny + 4ull * (1u << PART_MAX_BITS);
+  }
+  __device__ void bind(uint8_t* area, const GbParams& p) {
+    tk = (uint64_t*)area;
+    cnt = (unsigned int*)(tk + p.tiny_slots);
+  }
+  __device__ void init(const GbParams& p) {
+    for (uint32_t i = threadIdx.x; i < p.tiny_slots; i += GB_BLOCK) tk[i] = p.tiny_init[i];
+    for (uint32_t i = threadIdx.x; i < (1u << p.part_bits); i += GB_BLOCK) cnt[i] = 0;
+  }
+  __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>&) {
+    if (!is_pinned(p, tk, ek)) atomicAdd(&cnt[part_of(ek, p.part_bits)], 1u);
+    return true;
+  }
+  __device__ void flush(const GbParams& p) {
+    named_sync(GB_BLOCK);
+    for (uint32_t i = threadIdx.x; i < (1u << p.part_bits); i += GB_BLOCK)
+      p.hist[(size_t)i * p.fixed_grid + blockIdx.x] = cnt[i];
+  }
+};
+
+// Pass 2: pinned keys aggregate in thread-private slots (merged into the
+// global table at the end); every other row becomes a (key, value) record
+// at its partition's next position for this CTA.
+template <class S>
+struct BePartScatter {
+  static constexpr int A = S::A;
+  static constexpr int ID = relhost::K_GB_PSCATTER;
+  static constexpr int SIDE = SIDE_AGG;
+  BeLayered<S> hot;           // thread-private layer (frozen) only
+  unsigned long long* cursor; // [P] next record index of this CTA per partition
+  unsigned long long total;   // records the histogram counted (bound check)
+  __host__ __device__ static uint64_t bytes(uint32_t tiny, uint32_t) {
+    return ((BeLayered<S>::bytes(tiny, 0) + 15) & ~15ull) + 8ull * (1u << PART_MAX_BITS);
+  }
+  __device__ void bind(uint8_t* area, const GbParams& p) {
+    hot.bind(area, p);
+    cursor = (unsigned long long*)(area + ((BeLayered<S>::bytes(p.tiny_slots, 0) + 15) & ~15ull));
+  }
+  __device__ void init(const GbParams& p) {
+    hot.init(p);
+    for (uint32_t i = threadIdx.x; i < (1u << p.part_bits); i += GB_BLOCK)
+      cursor[i] = p.part_start[i] + p.hist[(size_t)i * p.fixed_grid + blockIdx.x];
+    total = p.part_start[1u << p.part_bits];
+  }
+  __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>& x) {
+    if (p.tiny_frozen) {
+      const uint32_t s = small_slot_of(ek, p.tiny_slots - 1, p.tiny_mult);
+      if (hot.tk[s] == ek) {
+        hot.seen |= 1u << s;
+        hot.tiny_rmw(p, s, x);
+        return true;
+      }
+    }
+    const unsigned long long pos = atomicAdd(&cursor[part_of(ek, p.part_bits)], 1ull);
+    if (pos >= total) {  // the passes disagreed: report, never write past the buffer
+      atomicOr(&p.hdr->timeout, 2u);
+      return false;
+    }
+    PartRec r;
+    r.ek = ek;
+    r.val = (long long)x.v[0];
+    p.recs[pos] = r;
+    return true;
+  }
+  __device__ void flush(const GbParams& p) { hot.flush(p); }
+};
+
 // Distinct-key counting: a CTA-shared key filter in front of the global set.
 template <class S>
 struct BeKeySet {
   static constexpr int A = S::A;
   static constexpr int ID = relhost::K_GB_KEYSET;
+  static constexpr int SIDE = SIDE_COUNT;
   uint64_t* tk;
   __host__ __device__ static uint64_t bytes(uint32_t, uint32_t shared) { return 8ull * shared; }
   __device__ void bind(uint8_t* area, const GbParams&) { tk = (uint64_t*)area; }
@@ -586,9 +683,9 @@ __device__ __forceinline__ bool run_rows(const GbParams& p, BE& be, const V& v, 
     uint64_t ek;
     Vals<S::A> x;
     if (!S::row(p, q, r, ek, x)) continue;
-    if (ek == 0) {  // the key INT64_MIN: side accumulator
-      atomicAdd(&p.hdr->n_side, 1ull);
-      if (!KEYSET) red_words<S>(p, p.hdr->side_aggs, x);
+    if (ek == 0) {  // the key INT64_MIN: side accumulator (once per row overall)
+      if (BE::SIDE != SIDE_SKIP) atomicAdd(&p.hdr->n_side, 1ull);
+      if (BE::SIDE == SIDE_AGG) red_words<S>(p, p.hdr->side_aggs, x);
       continue;
     }
     ok &= be.update(p, ek, x);
@@ -734,6 +831,214 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_compact(const __grid_constant__ G
   }
 }
 
+// ------------------------------------------- partitioned variant: scan, agg
+
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
+__device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long* total) {
+  __shared__ unsigned long long warp_sum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long w = lane < nw ? warp_sum[lane] : 0;
+    unsigned long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nw) warp_sum[lane] = wi - w;  // exclusive prefix of warp totals
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  const unsigned long long r = warp_sum[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+// hist[part][cta] -> exclusive offsets inside the partition; the partition's
+// total goes to part_start[part].  One CTA per partition.
+__global__ void __launch_bounds__(1024) gb_part_scan1(const __grid_constant__ GbParams p) {
+  __shared__ unsigned long long total;
+  const uint32_t G = p.fixed_grid;
+  uint32_t* h = p.hist + (size_t)blockIdx.x * G;
+  const uint32_t per = (G + blockDim.x - 1) / blockDim.x;
+  const uint32_t b = threadIdx.x * per, e = b + per < G ? b + per : G;
+  unsigned long long s = 0;
+  for (uint32_t i = b; i < e; ++i) s += h[i];
+  unsigned long long run = block_exclusive_scan(s, &total);
+  for (uint32_t i = b; i < e; ++i) {
+    const uint32_t v = h[i];
+    h[i] = (uint32_t)run;
+    run += v;
+  }
+  if (threadIdx.x == 0) p.part_start[blockIdx.x] = total;
+}
+
+// partition totals -> first record of each partition; part_start[P] = all.
+__global__ void __launch_bounds__(1024) gb_part_scan2(const __grid_constant__ GbParams p) {
+  __shared__ unsigned long long total;
+  const uint32_t P = 1u << p.part_bits;
+  const uint32_t per = (P + blockDim.x - 1) / blockDim.x;
+  const uint32_t b = threadIdx.x * per, e = b + per < P ? b + per : P;
+  unsigned long long s = 0;
+  for (uint32_t i = b; i < e; ++i) s += p.part_start[i];
+  unsigned long long run = block_exclusive_scan(s, &total);
+  for (uint32_t i = b; i < e; ++i) {
+    const unsigned long long v = p.part_start[i];
+    p.part_start[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) p.part_start[P] = total;
+}
+
+// Insert-or-accumulate into a partition's shared-memory table; a key that
+// finds no slot within 32 probes goes to the global table and marks the
+// partition as spilled.
+template <class S>
+__device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, unsigned long long* ta,
+                                            uint32_t TS, uint64_t ek, const Vals<S::A>& x,
+                                            int* ovf) {
+  uint32_t s = small_slot_of(ek, TS - 1, SHARED_MULT);
+  for (uint32_t k = 0; k < 32; ++k) {
+    uint64_t cur = *(volatile uint64_t*)(tk + s);
+    if (cur == 0) {
+      cur = atomicCAS((unsigned long long*)(tk + s), 0ull, (unsigned long long)ek);
+      if (cur == 0) cur = ek;
+    }
+    if (cur == ek) {
+      red_words<S>(p, ta + (size_t)s * S::A, x);
+      return;
+    }
+    s = (s + 1) & (TS - 1);
+  }
+  *(volatile int*)ovf = 1;
+  gtab_update<S>(p, ek, x);
+}
+
+// Pass 3: each CTA aggregates whole partitions in a shared-memory table of
+// p.smem_slots slots and writes their groups straight to the output (warp
+// ballot / popc, one atomic per warp).  Every key lives in one partition, so
+// no group is emitted twice -- unless the table overflows: then the whole
+// partition is merged into the global table instead, which the compaction
+// kernel emits afterwards.
+template <class S>
+__global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ GbParams p,
+                                                         const __grid_constant__ GbOut o) {
+  constexpr int A = S::A;
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ int ovf;
+  const uint32_t TS = p.smem_slots;
+  uint64_t* tk = (uint64_t*)sm;
+  unsigned long long* ta = (unsigned long long*)(tk + TS);
+  const uint32_t P = 1u << p.part_bits;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  // a partition far above the average (skewed keys) is split into up to
+  // PART_CHUNKS chunks on different CTAs, which then merge into the global
+  // table instead of emitting
+  const unsigned long long avg = p.part_start[P] / P;
+  const unsigned long long chunk_min = 4 * avg > 4096 ? 4 * avg : 4096;
+  for (uint32_t item = blockIdx.x; item < P * PART_CHUNKS; item += gridDim.x) {
+    // chunk-major numbering: the first chunks of all partitions come first and
+    // spread over every CTA
+    const uint32_t part = item % P, c = item / P;
+    const unsigned long long pb = p.part_start[part], pe = p.part_start[part + 1];
+    const unsigned long long size = pe - pb;
+    unsigned long long nch = (size + chunk_min - 1) / chunk_min;
+    nch = nch < 1 ? 1 : (nch > PART_CHUNKS ? PART_CHUNKS : nch);
+    if (c >= nch) continue;  // uniform across the CTA
+    const unsigned long long beg = pb + size * c / nch, end = pb + size * (c + 1) / nch;
+    for (uint32_t i = threadIdx.x; i < TS * (1 + A); i += GB_BLOCK) tk[i] = 0;
+    if (threadIdx.x == 0) ovf = nch > 1;
+    __syncthreads();
+    if (nch == 1) {
+      for (unsigned long long i = beg + threadIdx.x; i < end; i += GB_BLOCK) {
+        const PartRec r = p.recs[i];
+        Vals<A> x;
+        S::from_val((uint64_t)r.val, x);
+        part_insert<S>(p, tk, ta, TS, r.ek, x, &ovf);
+      }
+    } else {
+      // heavy chunk, few distinct keys per warp: combine each key's rows in
+      // the warp first (0 is every word's identity), then one table update
+      const int warp = threadIdx.x >> 5;
+      for (unsigned long long b0 = beg + (unsigned long long)warp * 32; b0 < end; b0 += GB_BLOCK) {
+        const unsigned long long i = b0 + lane;
+        const bool valid = i < end;
+        Vals<A> x;
+        uint64_t ek = 0;
+        if (valid) {
+          const PartRec r = p.recs[i];
+          ek = r.ek;
+          S::from_val((uint64_t)r.val, x);
+        } else {
+#pragma unroll
+          for (int a = 0; a < A; ++a) x.v[a] = 0;
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, valid);
+        while (pend) {
+          const int ld = __ffs(pend) - 1;
+          const uint64_t key = __shfl_sync(0xffffffffu, ek, ld);
+          const bool mine = valid && ek == key;
+          const unsigned m = __ballot_sync(0xffffffffu, mine);
+          Vals<A> y;
+#pragma unroll
+          for (int a = 0; a < A; ++a) {
+            const bool um = is_umax<S>(p, a);
+            uint64_t v = mine ? x.v[a] : 0ull;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+              const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+              v = um ? (v > w ? v : w) : v + w;
+            }
+            y.v[a] = v;
+          }
+          if (lane == ld) part_insert<S>(p, tk, ta, TS, key, y, &ovf);
+          pend &= ~m;
+        }
+      }
+    }
+    __syncthreads();
+    const bool spill = ovf != 0;
+    for (uint32_t base = 0; base < TS; base += GB_BLOCK) {
+      const uint32_t s = base + threadIdx.x;
+      const uint64_t ek = s < TS ? tk[s] : 0;
+      const bool occ = ek != 0;
+      if (spill) {  // partition did not fit: everything to the global table
+        if (occ) {
+          Vals<A> x;
+#pragma unroll
+          for (int a = 0; a < A; ++a) x.v[a] = ta[(size_t)s * A + a];
+          gtab_update<S>(p, ek, x);
+        }
+        continue;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, occ);
+      if (!m) continue;
+      unsigned long long wb = 0;
+      if (lane == 0) wb = atomicAdd(&p.hdr->n_out, (unsigned long long)__popc(m));
+      wb = __shfl_sync(0xffffffffu, wb, 0);
+      if (occ) {
+        const uint64_t pos = wb + __popc(m & lt);
+        if (pos < (uint64_t)o.capacity) {
+          o.keys[pos] = (int64_t)(ek ^ KEY_FLIP);
+#pragma unroll
+          for (int a = 0; a < A; ++a) o.aggs[a][pos] = agg_decode(p.aop[a], ta[(size_t)s * A + a]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ launch
 
 namespace {
@@ -761,6 +1066,17 @@ auto with_keyset_shape(int shape, F&& f) {
     case SHAPE_KVRT64: case SHAPE_KV4_64: case SHAPE_KV2_64: return f(ShapeKVRT<int64_t>{});
     case SHAPE_KVRT32: case SHAPE_KV4_32: case SHAPE_KV2_32: return f(ShapeKVRT<int32_t>{});
     default: return f(ShapeGeneric{});
+  }
+}
+
+// Partitioned passes: key + int64 value shapes only.
+template <class F>
+auto with_part_shape(int shape, F&& f) {
+  switch (shape) {
+    case SHAPE_KV4_32: return f(ShapeKV<int32_t, 4>{});
+    case SHAPE_KV2_64: return f(ShapeKV<int64_t, 2>{});
+    case SHAPE_KV2_32: return f(ShapeKV<int32_t, 2>{});
+    default: return f(ShapeKV<int64_t, 4>{});
   }
 }
 
@@ -812,6 +1128,7 @@ rel_status launch_one(const GbParams& p, cudaStream_t st) {
   const int64_t tiles = (p.n_rows + p.tile_rows - 1) / p.tile_rows;
   int64_t grid = (int64_t)relhost::device_sms() * per_sm;
   if (grid > tiles) grid = tiles > 0 ? tiles : 1;
+  if (p.fixed_grid) grid = p.fixed_grid;  // passes that must map rows to CTAs alike
   relhost::launch_begin(BE::ID, st);
   kern<<<(unsigned)grid, GB_THREADS, smem, st>>>(p);
   relhost::launch_end(BE::ID, st);
@@ -828,6 +1145,14 @@ int gb_shape_width(int shape) {
 
 uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t tiny_slots, uint32_t smem_slots) {
   if (mode == MODE_KEYSET) return 8ull * smem_slots;
+  if (mode == MODE_PHIST)
+    return with_part_shape(shape, [&](auto s) {
+      return BePartHist<decltype(s)>::bytes(tiny_slots, smem_slots);
+    });
+  if (mode == MODE_PSCATTER)
+    return with_part_shape(shape, [&](auto s) {
+      return BePartScatter<decltype(s)>::bytes(tiny_slots, smem_slots);
+    });
   if (mode == MODE_TINY)
     return with_regs(shape, 8, [&](auto be) { return decltype(be)::bytes(tiny_slots, smem_slots); });
   return with_shape(shape, [&](auto s) {
@@ -836,6 +1161,15 @@ uint64_t gb_backend_smem_bytes(int mode, int shape, uint32_t tiny_slots, uint32_
 }
 
 int gb_ctas_per_sm(const GbParams& p, int shape, int mode, bool tma) {
+  if (mode == MODE_PHIST || mode == MODE_PSCATTER)
+    return with_part_shape(shape, [&](auto s) {
+      using S = decltype(s);
+      if (mode == MODE_PHIST)
+        return tma ? occupancy<S, BePartHist<S>, false, true>(p)
+                   : occupancy<S, BePartHist<S>, false, false>(p);
+      return tma ? occupancy<S, BePartScatter<S>, false, true>(p)
+                 : occupancy<S, BePartScatter<S>, false, false>(p);
+    });
   if (mode == MODE_KEYSET)
     return with_keyset_shape(shape, [&](auto s) {
       using S = decltype(s);
@@ -856,7 +1190,16 @@ int gb_ctas_per_sm(const GbParams& p, int shape, int mode, bool tma) {
 }
 
 rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool tma, cudaStream_t st) {
-  if (p.n_rows == 0) return REL_OK;
+  if (p.n_rows == 0 && !p.fixed_grid) return REL_OK;
+  if (mode == MODE_PHIST || mode == MODE_PSCATTER)
+    return with_part_shape(shape, [&](auto s) {
+      using S = decltype(s);
+      if (mode == MODE_PHIST)
+        return tma ? launch_one<S, BePartHist<S>, false, true>(p, st)
+                   : launch_one<S, BePartHist<S>, false, false>(p, st);
+      return tma ? launch_one<S, BePartScatter<S>, false, true>(p, st)
+                 : launch_one<S, BePartScatter<S>, false, false>(p, st);
+    });
   if (mode == MODE_KEYSET)
     return with_keyset_shape(shape, [&](auto s) {
       using S = decltype(s);
@@ -873,6 +1216,38 @@ rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool tma, cuda
     using S = decltype(s);
     return tma ? launch_one<S, BeLayered<S>, false, true>(p, st)
                : launch_one<S, BeLayered<S>, false, false>(p, st);
+  });
+}
+
+rel_status gb_launch_part_scan(const GbParams& p, cudaStream_t st) {
+  const uint32_t P = 1u << p.part_bits;
+  relhost::launch_begin(relhost::K_GB_PSCAN, st);
+  gb_part_scan1<<<P, 1024, 0, st>>>(p);
+  gb_part_scan2<<<1, 1024, 0, st>>>(p);
+  relhost::launch_end(relhost::K_GB_PSCAN, st);
+  relhost::count_launch(1);  // two kernels, one profile record
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(partition scan)");
+}
+
+rel_status gb_launch_part_agg(const GbParams& p, int shape, const GbOut& o, cudaStream_t st) {
+  return with_part_shape(shape, [&](auto s) -> rel_status {
+    using S = decltype(s);
+    auto kern = gb_part_agg<S>;
+    const size_t smem = 8ull * p.smem_slots * (1 + S::A);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(partition agg)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GB_BLOCK, smem);
+    if (e != cudaSuccess || per_sm < 1) return relhost::cuda_fail(e, "occupancy(partition agg)");
+    const uint32_t P = 1u << p.part_bits;
+    uint32_t grid = (uint32_t)relhost::device_sms() * (uint32_t)per_sm;
+    if (grid > P) grid = P;
+    relhost::launch_begin(relhost::K_GB_PAGG, st);
+    kern<<<grid, GB_BLOCK, smem, st>>>(p, o);
+    relhost::launch_end(relhost::K_GB_PAGG, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(partition agg)");
   });
 }
 

@@ -13,7 +13,24 @@ constexpr int GB_SMEM_HEAD = 256;  // full[8] and empty[8] mbarriers, abort flag
 constexpr int TINY_MAX_SLOTS = 32;
 constexpr int SHARED_MAX_SLOTS = 4096;
 
-enum GbMode : int { MODE_LAYERED = 0, MODE_KEYSET = 1, MODE_TINY = 2 };
+enum GbMode : int {
+  MODE_LAYERED = 0,
+  MODE_KEYSET = 1,
+  MODE_TINY = 2,
+  MODE_PHIST = 3,     // partitioned: count rows per (partition, CTA)
+  MODE_PSCATTER = 4   // partitioned: write rows into their partitions
+};
+
+// What a pass does with rows whose key is INT64_MIN (they bypass tables).
+enum SideMode : int { SIDE_AGG = 0, SIDE_COUNT = 1, SIDE_SKIP = 2 };
+
+// Partitioned group-by record: the stored key and the row's raw value.
+struct alignas(16) PartRec {
+  unsigned long long ek;
+  long long val;
+};
+constexpr int PART_MAX_BITS = 13;  // at most 8192 partitions
+constexpr int PART_CHUNKS = 16;    // CTAs that may share one oversized partition
 
 // Row shapes.  The specialised ones fix column types and aggregate kinds at
 // compile time; KV4 / KV2 hold their aggregates in the internal order
@@ -62,6 +79,12 @@ struct GbParams {
   uint64_t tiny_dense;     // register mode: 4-bit dense id of each of <= 16 slots
   uint32_t tiny_ns;        // register mode: dense slots compiled in (4 or 8)
   int32_t req_tile, req_stages;  // staging chosen by the plan (0: automatic)
+  // partitioned variant
+  uint32_t part_bits;       // log2 of the partition count
+  uint32_t fixed_grid;      // CTAs of the histogram and scatter passes (equal)
+  uint32_t* hist;           // [P][fixed_grid] counts, then exclusive offsets
+  unsigned long long* part_start;  // [P + 1] first record of each partition
+  PartRec* recs;            // records of every non-pinned row
   // global table (or key set in MODE_KEYSET)
   uint64_t* tkeys;
   unsigned long long* taggs;  // slots x n_aggs words
@@ -80,6 +103,9 @@ struct GbOut {
 rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool use_tma,
                           cudaStream_t st);
 rel_status gb_launch_compact(const GbParams& p, const GbOut& o, cudaStream_t st);
+// Partitioned variant: offsets from the histogram, then per-partition tables.
+rel_status gb_launch_part_scan(const GbParams& p, cudaStream_t st);
+rel_status gb_launch_part_agg(const GbParams& p, int shape, const GbOut& o, cudaStream_t st);
 // Aggregate-array width the kernel for a shape is compiled with.
 int gb_shape_width(int shape);
 // Shared-memory bytes of the per-CTA tables (before the staging ring).

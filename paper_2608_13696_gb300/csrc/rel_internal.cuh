@@ -192,7 +192,11 @@ enum KernelId : int {
   K_JOIN_COUNT = 5,
   K_SKETCH = 6,
   K_GB_REGS = 7,
-  K_COUNT_IDS = 8
+  K_GB_PHIST = 8,
+  K_GB_PSCAN = 9,
+  K_GB_PSCATTER = 10,
+  K_GB_PAGG = 11,
+  K_COUNT_IDS = 12
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

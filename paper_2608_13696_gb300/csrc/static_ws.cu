@@ -72,6 +72,15 @@ extern "C" rel_status rel_groupby_agg_static(const rel_groupby_desc* desc, int64
   rel_plan plan;
   rel_status r = rel_plan_size(REL_OP_GROUPBY, desc, 0u, max_groups, nullptr, 0, &plan, stream);
   if (r != REL_OK) return r;
+  if (plan.variant == REL_VAR_PARTITIONED) {
+    // the partitioned variant keeps a record per input row: too much for a
+    // fixed array, so stay with the layered single table
+    plan.variant = REL_VAR_GLOBAL;
+    plan.part_bits = 0;
+    plan.tiny_slots = 8;
+    plan.smem_slots = 2048;
+    plan.workspace_bytes = rel_groupby_ws_bytes(plan.slots, desc->n_aggs);
+  }
   if (plan.workspace_bytes > STATIC_WS_BYTES) {
     relhost::set_error("static group-by: plan needs %llu bytes, scratch holds %zu",
                        (unsigned long long)plan.workspace_bytes, STATIC_WS_BYTES);

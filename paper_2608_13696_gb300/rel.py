@@ -71,7 +71,8 @@ class Plan(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("tiny_slots", ctypes.c_int32),
                 ("tiny_mult", ctypes.c_uint32), ("n_hot", ctypes.c_int32),
                 ("hot_keys", ctypes.c_int64 * 32), ("tile_rows", ctypes.c_int32),
-                ("n_stages", ctypes.c_int32)]
+                ("n_stages", ctypes.c_int32), ("part_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"Plan(slots={self.slots}, variant={self.variant}, tiny_slots={self.tiny_slots}, "
@@ -117,7 +118,7 @@ _lib = None
 EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join_ws_bytes",
            "rel_join_build", "rel_join_probe", "rel_last_error", "rel_launch_count",
            "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name",
-           "rel_groupby_agg_static", "rel_sketch", "rel_sketch_ws_bytes"]
+           "rel_groupby_agg_static", "rel_sketch", "rel_sketch_ws_bytes", "rel_plan_ws_bytes"]
 SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
 
@@ -166,6 +167,8 @@ def load(build_if_stale: bool = True):
         L.rel_profile_stop.argtypes = [vp, vp, i64]
         L.rel_kernel_name.restype = ctypes.c_char_p
         L.rel_kernel_name.argtypes = [i32]
+        L.rel_plan_ws_bytes.restype = u64
+        L.rel_plan_ws_bytes.argtypes = [ctypes.POINTER(Plan), i32, i64]
         L.rel_sketch_ws_bytes.restype = u64
         L.rel_sketch_ws_bytes.argtypes = []
         L.rel_sketch.restype = i32
@@ -271,8 +274,9 @@ def groupby(q: dict, plan: Plan | None = None, flags: int = 0, groups_hint: int 
         plan = plan_groupby(q, flags=flags, groups_hint=groups_hint, stream=stream)
     if capacity is None:
         capacity = max(1, plan.est_groups + 1)
-    if ws is None or ws.numel() < plan.workspace_bytes:
-        ws = _ws(plan.workspace_bytes, dev)
+    need = int(L.rel_plan_ws_bytes(ctypes.byref(plan), d.n_aggs, d.d.n_rows))
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, dev)
     st = _stream(stream)
     while True:
         keys = torch.empty(capacity, dtype=torch.int64, device=dev)

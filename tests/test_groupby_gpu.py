@@ -204,7 +204,7 @@ def test_full_size_zipf_200m():
     keys, vals = synth.zipf_kv(N_BIG, seed=0)
     sample = np.array([synth.mix64_signed(r) for r in (1, 2, 3, 10, 1000, 10**5, 10**6)])
     plan = _big_checks(keys, vals, rel.PLAN_EXACT, sample)
-    assert plan.variant == rel.VAR_GLOBAL
+    assert plan.variant == rel.VAR_PARTITIONED
 
 
 def test_full_size_four_keys_200m():
