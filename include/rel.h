@@ -114,9 +114,22 @@ typedef struct {
 
 /* plan flags */
 #define REL_PLAN_EXACT 1u   /* count distinct qualifying keys exactly (GPU pre-pass) */
-#define REL_PLAN_LEARNED 2u /* reserved: sample sketch + learned size / variant      */
+#define REL_PLAN_LEARNED 2u /* sample sketch + planner network: size and variant     */
 #define REL_PLAN_GENERIC 4u /* force the descriptor-interpreting kernel              */
 #define REL_PLAN_SKETCH 8u  /* sample sketch: heavy hitters pinned per CTA           */
+/* Force a variant (bits 8..9 of flags; 0 = the planner's choice):
+ * REL_PLAN_FORCE(REL_VAR_SMEM): per-CTA table of next_pow2(2 * est) slots
+ *   (at most 4096; what does not fit spills to the global table);
+ * REL_PLAN_FORCE(REL_VAR_GLOBAL): no per-CTA layer, every row updates the
+ *   global table;
+ * REL_PLAN_FORCE(REL_VAR_PARTITIONED): partitioned; only for one int32 or
+ *   int64 key, no filter, and SUM, COUNT (and MIN, MAX) of one int64 value
+ *   column, with fewer than 2^32 rows (REL_E_UNSUPPORTED otherwise). */
+#define REL_PLAN_FORCE(v) ((uint32_t)(v) << 8)
+#define REL_PLAN_FORCE_MASK 0x300u
+/* Set in plan->flags by rel_groupby_auto when the first plan overflowed and
+ * the call re-planned with the exact pre-pass. */
+#define REL_PLAN_FELL_BACK 0x10000u
 
 #define REL_MAX_HOT 32
 
@@ -156,6 +169,14 @@ typedef struct {
  *      plan->scratch_bytes of ws (query with ws = NULL: returns
  *      REL_E_CAPACITY after filling scratch_bytes);
  *    otherwise: size for n_rows groups (always sufficient, rarely economical).
+ *    flags & REL_PLAN_LEARNED (without a hint or REL_PLAN_EXACT): run
+ *      rel_sketch, then the registered planner network (rel_planner_set) on
+ *      its features; est_groups = max(ceil(1.25 * 2^y0), sample distinct
+ *      keys), the variant is the network's most likely one that the
+ *      descriptor supports.  Needs rel_sketch_ws_bytes() + 2048 bytes of ws
+ *      and returns REL_E_INVALID when no network is registered.  An estimate
+ *      can be too low: rel_groupby_agg then returns REL_E_OVERFLOW
+ *      (rel_groupby_auto re-plans exactly).
  *    flags & REL_PLAN_SKETCH (with any of the above): also run rel_sketch and
  *      pin the sample's most frequent keys in the thread-private slots (all
  *      of them when the sample suggests few groups, the heavy hitters when it
@@ -194,6 +215,23 @@ uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs);
  * n_rows rows with n_aggs aggregates -- the partitioned variant also keeps a
  * 16-byte record per row. */
 uint64_t rel_plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows);
+
+/* Plan and run in one call, with the learned planner's overflow fallback:
+ * plan with `flags` (as rel_plan_size with groups_hint 0), run; when the run
+ * overflows a plan that was not exact, plan again with REL_PLAN_EXACT
+ * (keeping REL_PLAN_SKETCH, REL_PLAN_GENERIC and a forced variant) and run
+ * again.  ws must hold rel_groupby_auto_ws_bytes(desc) bytes (enough for any
+ * plan of desc).  plan_out (host, may be NULL) receives the plan that gave
+ * the result, REL_PLAN_FELL_BACK set in its flags after a re-plan.  Outputs
+ * and return codes as rel_groupby_agg; REL_E_CAPACITY before any device work
+ * when ws is smaller than stated. */
+rel_status rel_groupby_auto(const rel_groupby_desc* desc, uint32_t flags, void* ws,
+                            size_t ws_bytes, int64_t* out_keys, int64_t* const* out_aggs,
+                            int64_t out_capacity, int64_t* n_groups_host, rel_plan* plan_out,
+                            void* stream);
+
+/* Device bytes rel_groupby_auto needs for desc (0 for an invalid desc). */
+uint64_t rel_groupby_auto_ws_bytes(const rel_groupby_desc* desc);
 
 /* ------------------------------------------------------ sample sketch */
 
@@ -256,6 +294,52 @@ rel_status rel_sketch(const rel_groupby_desc* desc, void* ws, size_t ws_bytes,
 rel_status rel_groupby_agg_static(const rel_groupby_desc* desc, int64_t max_groups,
                                   int64_t* out_keys, int64_t* const* out_aggs,
                                   int64_t out_capacity, int64_t* n_groups_host, void* stream);
+
+/* ---------------------------------------------------- planner network */
+
+/* A small network maps a sketch's 264 features to an estimate of log2(number
+ * of groups) and logits over three group-by variants (REL_VAR_SMEM,
+ * REL_VAR_GLOBAL, REL_VAR_PARTITIONED).  The paper has no planner; this is
+ * the sizing step learned from runs of this library.  264 -> 64 -> 64 -> 4,
+ * ReLU hidden layers, BF16 weights and activations multiplied with FP32
+ * accumulation.  Parameters (FP32 master copy, and a BF16 copy of the same
+ * layout) in order: W1[64][264] b1[64] W2[64][64] b2[64] W3[4][64] b3[4].
+ * Every pointer below is device memory owned by the caller. */
+#define REL_MLP_IN 264
+#define REL_MLP_HIDDEN 64
+#define REL_MLP_OUT 4
+#define REL_MLP_PARAMS 21380
+
+/* bf16_params[i] = round-to-nearest-even BF16 of params[i]. */
+rel_status rel_mlp_round(const float* params, void* bf16_params, void* stream);
+
+/* out[b][0..4) for b < batch; x is batch x 264 FP32 (rounded to BF16 on
+ * entry).  acts (batch x 128 floats) receives the hidden pre-activations for
+ * rel_mlp_backward, or is NULL. */
+rel_status rel_mlp_forward(const void* bf16_params, const float* params, const float* x,
+                           int32_t batch, float* out, float* acts, void* stream);
+
+/* Scratch bytes rel_mlp_backward needs for a batch. */
+uint64_t rel_mlp_ws_bytes(int32_t batch);
+
+/* Gradient of the batch-mean loss (y0 - t_ndv)^2 + CE(softmax(y1..3), t_var)
+ * with respect to every parameter (grad: REL_MLP_PARAMS floats, overwritten);
+ * *loss (device float) receives the batch-mean loss.  x, acts and out as
+ * produced by rel_mlp_forward; t_var in {0, 1, 2}. */
+rel_status rel_mlp_backward(const void* bf16_params, const float* x, const float* acts,
+                            const float* out, const float* t_ndv, const int32_t* t_var,
+                            int32_t batch, void* ws, size_t ws_bytes, float* grad, float* loss,
+                            void* stream);
+
+/* One AdamW step (decoupled weight decay on weights, not biases; bias-
+ * corrected moments m, v; step >= 1), then refresh the BF16 copy. */
+rel_status rel_mlp_adamw(float* params, void* bf16_params, float* m, float* v, const float* grad,
+                         int32_t step, float lr, float beta1, float beta2, float eps,
+                         float weight_decay, void* stream);
+
+/* Register the network REL_PLAN_LEARNED plans with (device pointers, kept by
+ * reference; NULL clears).  Not thread-safe against concurrent planning. */
+rel_status rel_planner_set(const void* bf16_params, const float* params);
 
 /* ----------------------------------------------------------------- join */
 

@@ -2,6 +2,7 @@
 // mapping of a descriptor onto a specialised kernel, and the launches.
 // Validation happens before any CUDA call, so a rejected request never
 // touches the device.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -13,6 +14,7 @@
 
 #include "groupby.cuh"
 #include "join.cuh"
+#include "mlp.cuh"
 #include "sketch.cuh"
 
 #include <cmath>
@@ -618,6 +620,73 @@ rel_status set_layers(GbParams& p, const rel_plan* plan, int shape) {
   return REL_OK;
 }
 
+// The network REL_PLAN_LEARNED consults (caller-owned device memory).
+const void* g_planner_bf16 = nullptr;
+const float* g_planner_f32 = nullptr;
+
+// Scratch after the sketch's: the 264 features and the 4 network outputs.
+constexpr uint64_t LEARN_SCRATCH = 2048;
+constexpr uint64_t LEARN_OUT_OFF = 1280;
+
+// The learned sizing step: sketch, network forward, estimate and variant.
+rel_status learned_estimate(const rel_groupby_desc* d, bool p_ok, void* ws, size_t ws_bytes,
+                            rel_sketch_info* info, int64_t* est, int* variant, cudaStream_t st) {
+  if (!g_planner_bf16) return set_error("plan: no planner network registered"), REL_E_INVALID;
+  const uint64_t sk = rel_sketch_ws_bytes();
+  rel_status r = rel_sketch(d, ws, ws_bytes, info, st);
+  if (r) return r;
+  float* dx = (float*)((uint8_t*)ws + sk);
+  float* dy = (float*)((uint8_t*)ws + sk + LEARN_OUT_OFF);
+  cudaError_t e = cudaMemcpyAsync(dx, info->features, sizeof info->features,
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemcpyAsync");
+  if ((r = mlp_forward(g_planner_bf16, g_planner_f32, dx, 1, dy, nullptr, st))) return r;
+  float y[REL_MLP_OUT];
+  e = cudaMemcpyAsync(y, dy, sizeof y, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the planner output");
+  // 25 % headroom over the predicted count; never below the distinct keys
+  // already seen in the sample, never above the rows
+  int64_t n = d->n_rows;
+  if (std::isfinite(y[0])) {
+    const double g = std::ceil(std::exp2(std::min(std::max((double)y[0], 0.0), 62.0)) * 1.25);
+    n = g < (double)d->n_rows ? (int64_t)g : d->n_rows;
+  }
+  if (n < info->ndv) n = info->ndv;
+  *est = n;
+  int best = REL_VAR_SMEM;
+  for (int v = REL_VAR_GLOBAL; v <= REL_VAR_PARTITIONED; ++v)
+    if ((v != REL_VAR_PARTITIONED || p_ok) && y[v] > y[best]) best = v;
+  *variant = best;
+  return REL_OK;
+}
+
+// Table layers for a variant (0 = the rule by group count).
+void choose_variant(int variant, int64_t est, int64_t n_rows, int words, bool p_ok,
+                    rel_plan* plan) {
+  switch (variant) {
+    case REL_VAR_SMEM:
+      choose_layers(est, words, plan);
+      if (plan->variant != REL_VAR_SMEM) {
+        plan->variant = REL_VAR_SMEM;
+        plan->smem_slots = SHARED_MAX_SLOTS;
+        plan->tiny_slots = words <= 6 ? 8 : 0;
+      }
+      break;
+    case REL_VAR_GLOBAL:
+      plan->variant = REL_VAR_GLOBAL;
+      plan->tiny_slots = 0;
+      plan->smem_slots = 0;
+      break;
+    case REL_VAR_PARTITIONED:
+      choose_partitioned(est, n_rows, plan);
+      break;
+    default:
+      choose_layers(est, words, plan);
+      if (plan->variant == REL_VAR_GLOBAL && p_ok) choose_partitioned(est, n_rows, plan);
+  }
+}
+
 rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint, void* ws,
                         size_t ws_bytes, rel_plan* plan, cudaStream_t st) {
   rel_status r = validate_desc(d);
@@ -627,9 +696,31 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
   GbParams p;
   Mapped m = match_shape(d, p);
   if (flags & REL_PLAN_GENERIC) m.shape = SHAPE_GENERIC;
+  const bool p_ok = part_shape(m.shape) && d->n_rows < (1ll << 32);
+  const int forced = (int)((flags & REL_PLAN_FORCE_MASK) >> 8);
+  if (forced == REL_VAR_PARTITIONED && !p_ok)
+    return set_error("plan: the partitioned variant needs one int32/int64 key, no filter, "
+                     "one value column and fewer than 2^32 rows"),
+           REL_E_UNSUPPORTED;
+  rel_sketch_info info;
+  bool have_info = false;
+  int learned = 0;
   int64_t est;
   if (hint > 0) {
     est = hint;
+  } else if ((flags & REL_PLAN_LEARNED) && !(flags & REL_PLAN_EXACT)) {
+    plan->scratch_bytes = rel_sketch_ws_bytes() + LEARN_SCRATCH;
+    if (!ws || ws_bytes < plan->scratch_bytes) {
+      set_error("plan: learned sizing needs %llu workspace bytes",
+                (unsigned long long)plan->scratch_bytes);
+      return REL_E_CAPACITY;
+    }
+    if (d->n_rows == 0) {
+      est = 0;
+    } else {
+      if ((r = learned_estimate(d, p_ok, ws, ws_bytes, &info, &est, &learned, st))) return r;
+      have_info = true;
+    }
   } else if (flags & REL_PLAN_EXACT) {
     const uint64_t set_slots = next_pow2((uint64_t)(2 * d->n_rows < 16 ? 16 : 2 * d->n_rows));
     plan->scratch_bytes = HEADER_BYTES + 8ull * set_slots;
@@ -702,20 +793,19 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
   }
   plan->est_groups = est;
   plan->slots = (int64_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
-  choose_layers(est, gb_shape_width(m.shape), plan);
-  if (plan->variant == REL_VAR_GLOBAL && part_shape(m.shape) && d->n_rows < (1ll << 32))
-    choose_partitioned(est, d->n_rows, plan);
+  choose_variant(forced ? forced : learned, est, d->n_rows, gb_shape_width(m.shape), p_ok, plan);
   plan->workspace_bytes = plan_ws_bytes(plan, d->n_aggs, d->n_rows);
   if ((flags & REL_PLAN_SKETCH) && d->n_rows > 0) {
-    const uint64_t need = rel_sketch_ws_bytes();
-    if (plan->scratch_bytes < need) plan->scratch_bytes = need;
-    if (!ws || ws_bytes < plan->scratch_bytes) {
-      set_error("plan: sketching needs %llu workspace bytes",
-                (unsigned long long)plan->scratch_bytes);
-      return REL_E_CAPACITY;
+    if (!have_info) {
+      const uint64_t need = rel_sketch_ws_bytes();
+      if (plan->scratch_bytes < need) plan->scratch_bytes = need;
+      if (!ws || ws_bytes < plan->scratch_bytes) {
+        set_error("plan: sketching needs %llu workspace bytes",
+                  (unsigned long long)plan->scratch_bytes);
+        return REL_E_CAPACITY;
+      }
+      if ((r = rel_sketch(d, ws, ws_bytes, &info, st))) return r;
     }
-    rel_sketch_info info;
-    if ((r = rel_sketch(d, ws, ws_bytes, &info, st))) return r;
     apply_sketch(info, gb_shape_width(m.shape), plan);
   }
   return REL_OK;
@@ -810,13 +900,73 @@ const char* rel_kernel_name(int32_t id) {
   static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
                                 "join_build", "join_probe", "join_count", "sketch", "gb_main_regs",
                                 "gb_part_hist", "gb_part_scan", "gb_part_scatter",
-                                "gb_part_agg"};
+                                "gb_part_agg", "mlp"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 
 uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs) {
   if (slots < 0 || n_aggs < 0) return 0;
   return gb_ws_bytes(slots, n_aggs);
+}
+
+// ---------------------------------------------------------- planner network
+
+rel_status rel_mlp_round(const float* params, void* bf16_params, void* stream) {
+  if (!params || !bf16_params) return set_error("mlp: NULL parameters"), REL_E_INVALID;
+  return mlp_round(params, bf16_params, as_stream(stream));
+}
+
+rel_status rel_mlp_forward(const void* bf16_params, const float* params, const float* x,
+                           int32_t batch, float* out, float* acts, void* stream) {
+  if (batch < 0) return set_error("mlp: batch < 0"), REL_E_INVALID;
+  if (batch > 0 && (!bf16_params || !params || !x || !out))
+    return set_error("mlp: NULL argument"), REL_E_INVALID;
+  return mlp_forward(bf16_params, params, x, batch, out, acts, as_stream(stream));
+}
+
+uint64_t rel_mlp_ws_bytes(int32_t batch) {
+  return batch < 0 ? 0 : sizeof(float) * (uint64_t)DZ_STRIDE * (uint64_t)(batch > 0 ? batch : 1);
+}
+
+rel_status rel_mlp_backward(const void* bf16_params, const float* x, const float* acts,
+                            const float* out, const float* t_ndv, const int32_t* t_var,
+                            int32_t batch, void* ws, size_t ws_bytes, float* grad, float* loss,
+                            void* stream) {
+  if (batch < 0) return set_error("mlp: batch < 0"), REL_E_INVALID;
+  if (!grad || !loss || (batch > 0 && (!bf16_params || !x || !acts || !out || !t_ndv || !t_var)))
+    return set_error("mlp: NULL argument"), REL_E_INVALID;
+  if (!ws || ws_bytes < rel_mlp_ws_bytes(batch))
+    return set_error("mlp: workspace needs %llu bytes",
+                     (unsigned long long)rel_mlp_ws_bytes(batch)),
+           REL_E_CAPACITY;
+  return mlp_backward(bf16_params, x, acts, out, t_ndv, t_var, batch, (float*)ws, grad, loss,
+                      as_stream(stream));
+}
+
+rel_status rel_mlp_adamw(float* params, void* bf16_params, float* m, float* v, const float* grad,
+                         int32_t step, float lr, float beta1, float beta2, float eps,
+                         float weight_decay, void* stream) {
+  if (!params || !bf16_params || !m || !v || !grad)
+    return set_error("mlp: NULL argument"), REL_E_INVALID;
+  if (step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return set_error("mlp: bad AdamW hyper-parameters"), REL_E_INVALID;
+  MlpAdamW h;
+  h.lr = lr;
+  h.beta1 = beta1;
+  h.beta2 = beta2;
+  h.eps = eps;
+  h.wd = weight_decay;
+  h.bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+  h.bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+  return mlp_adamw(params, bf16_params, m, v, grad, h, as_stream(stream));
+}
+
+rel_status rel_planner_set(const void* bf16_params, const float* params) {
+  if ((bf16_params == nullptr) != (params == nullptr))
+    return set_error("planner: give both parameter copies or neither"), REL_E_INVALID;
+  g_planner_bf16 = bf16_params;
+  g_planner_f32 = params;
+  return REL_OK;
 }
 
 uint64_t rel_plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows) {
@@ -828,6 +978,45 @@ uint64_t rel_plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows)
 }
 
 uint64_t rel_sketch_ws_bytes(void) { return (sizeof(DevSketch) + 255) & ~(uint64_t)255; }
+
+uint64_t rel_groupby_auto_ws_bytes(const rel_groupby_desc* d) {
+  if (!d || d->n_rows < 0 || d->n_aggs < 0 || d->n_aggs > REL_MAX_AGGS) return 0;
+  // every estimate is at most n_rows
+  const uint64_t n = (uint64_t)d->n_rows;
+  const uint64_t slots = next_pow2(2 * n < 16 ? 16 : 2 * n);
+  const uint64_t p_slots = next_pow2(n / 4 > 65536 ? n / 4 : 65536);
+  uint64_t need = gb_ws_bytes((int64_t)slots, d->n_aggs);
+  need = std::max(need, part_layout((int64_t)p_slots, d->n_aggs, PART_MAX_BITS, d->n_rows).end);
+  need = std::max(need, HEADER_BYTES + 8 * slots);  // exact pre-pass key set
+  need = std::max(need, rel_sketch_ws_bytes() + LEARN_SCRATCH);
+  return need;
+}
+
+rel_status rel_groupby_auto(const rel_groupby_desc* d, uint32_t flags, void* ws, size_t ws_bytes,
+                            int64_t* out_keys, int64_t* const* out_aggs, int64_t out_capacity,
+                            int64_t* n_groups_host, rel_plan* plan_out, void* stream) {
+  rel_status r = validate_desc(d);
+  if (r) return r;
+  const uint64_t need = rel_groupby_auto_ws_bytes(d);
+  if (!ws || ws_bytes < need)
+    return set_error("group-by: workspace needs %llu bytes", (unsigned long long)need),
+           REL_E_CAPACITY;
+  cudaStream_t st = as_stream(stream);
+  rel_plan plan;
+  if ((r = plan_groupby(d, flags, 0, ws, ws_bytes, &plan, st))) return r;
+  int64_t n = 0;
+  r = rel_groupby_agg(d, &plan, ws, ws_bytes, out_keys, out_aggs, out_capacity, &n, stream);
+  if (r == REL_E_OVERFLOW && !(plan.flags & REL_PLAN_EXACT)) {
+    const uint32_t f2 =
+        (flags & (REL_PLAN_SKETCH | REL_PLAN_GENERIC | REL_PLAN_FORCE_MASK)) | REL_PLAN_EXACT;
+    if ((r = plan_groupby(d, f2, 0, ws, ws_bytes, &plan, st))) return r;
+    plan.flags |= REL_PLAN_FELL_BACK;
+    r = rel_groupby_agg(d, &plan, ws, ws_bytes, out_keys, out_aggs, out_capacity, &n, stream);
+  }
+  if (n_groups_host) *n_groups_host = n;
+  if (plan_out) *plan_out = plan;
+  return r;
+}
 
 rel_status rel_sketch(const rel_groupby_desc* d, void* ws, size_t ws_bytes, rel_sketch_info* out,
                       void* stream) {

@@ -196,7 +196,8 @@ enum KernelId : int {
   K_GB_PSCAN = 9,
   K_GB_PSCATTER = 10,
   K_GB_PAGG = 11,
-  K_COUNT_IDS = 12
+  K_MLP = 12,
+  K_COUNT_IDS = 13
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

@@ -29,6 +29,15 @@ U8, I32, I64 = 0, 1, 2
 OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
 VAR_AUTO, VAR_SMEM, VAR_GLOBAL, VAR_PARTITIONED = 0, 1, 2, 3
 PLAN_EXACT, PLAN_LEARNED, PLAN_GENERIC, PLAN_SKETCH = 1, 2, 4, 8
+PLAN_FELL_BACK = 0x10000
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 264, 64, 4, 21380
+
+
+def plan_force(variant: int) -> int:
+    """Flag bits that force a group-by variant (VAR_SMEM / VAR_GLOBAL / VAR_PARTITIONED)."""
+    return variant << 8
+
+
 OP_GROUPBY, OP_JOIN_PROBE = 0, 1
 MAX_COLS, MAX_KEYS, MAX_PREDS, MAX_AGGS = 8, 4, 4, 8
 
@@ -118,7 +127,9 @@ _lib = None
 EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join_ws_bytes",
            "rel_join_build", "rel_join_probe", "rel_last_error", "rel_launch_count",
            "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name",
-           "rel_groupby_agg_static", "rel_sketch", "rel_sketch_ws_bytes", "rel_plan_ws_bytes"]
+           "rel_groupby_agg_static", "rel_sketch", "rel_sketch_ws_bytes", "rel_plan_ws_bytes",
+           "rel_groupby_auto", "rel_groupby_auto_ws_bytes", "rel_mlp_round", "rel_mlp_forward",
+           "rel_mlp_ws_bytes", "rel_mlp_backward", "rel_mlp_adamw", "rel_planner_set"]
 SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
 
@@ -178,6 +189,26 @@ def load(build_if_stale: bool = True):
         L.rel_groupby_agg_static.argtypes = [ctypes.POINTER(GroupByDesc), i64, vp,
                                              ctypes.POINTER(ctypes.c_void_p), i64,
                                              ctypes.POINTER(i64), vp]
+        L.rel_groupby_auto.restype = i32
+        L.rel_groupby_auto.argtypes = [ctypes.POINTER(GroupByDesc), u32, vp, ctypes.c_size_t, vp,
+                                       ctypes.POINTER(ctypes.c_void_p), i64, ctypes.POINTER(i64),
+                                       ctypes.POINTER(Plan), vp]
+        L.rel_groupby_auto_ws_bytes.restype = u64
+        L.rel_groupby_auto_ws_bytes.argtypes = [ctypes.POINTER(GroupByDesc)]
+        L.rel_mlp_round.restype = i32
+        L.rel_mlp_round.argtypes = [vp, vp, vp]
+        L.rel_mlp_forward.restype = i32
+        L.rel_mlp_forward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.rel_mlp_ws_bytes.restype = u64
+        L.rel_mlp_ws_bytes.argtypes = [i32]
+        L.rel_mlp_backward.restype = i32
+        L.rel_mlp_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, ctypes.c_size_t, vp, vp,
+                                       vp]
+        L.rel_mlp_adamw.restype = i32
+        L.rel_mlp_adamw.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
+        L.rel_planner_set.restype = i32
+        L.rel_planner_set.argtypes = [vp, vp]
         _lib = L
         return L
 
@@ -311,6 +342,111 @@ def groupby_static(q: dict, max_groups: int, capacity: int | None = None, stream
                                     ctypes.byref(n), _stream(stream)))
     g = n.value
     return keys[:g], [a[:g] for a in aggs]
+
+
+def groupby_auto(q: dict, flags: int = 0, capacity: int | None = None,
+                 ws: torch.Tensor | None = None, stream=None):
+    """rel_groupby_auto: plan (flags as plan_groupby) and run in one call; an
+    overflowing learned plan is re-planned exactly.  Returns (keys, aggs, plan).
+    Default output capacity: one row per input row (always sufficient)."""
+    L = load()
+    d = _Desc(q)
+    dev = q["cols"][0].device
+    need = int(L.rel_groupby_auto_ws_bytes(ctypes.byref(d.d)))
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, dev)
+    cap = max(1, d.d.n_rows if capacity is None else capacity)
+    keys = torch.empty(cap, dtype=torch.int64, device=dev)
+    aggs = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in range(d.n_aggs)]
+    ptrs = (ctypes.c_void_p * max(1, d.n_aggs))(*[a.data_ptr() for a in aggs])
+    n = ctypes.c_int64(0)
+    plan = Plan()
+    _check(L.rel_groupby_auto(ctypes.byref(d.d), flags, ws.data_ptr(), ws.numel(),
+                              keys.data_ptr(), ptrs, cap, ctypes.byref(n), ctypes.byref(plan),
+                              _stream(stream)))
+    g = n.value
+    return keys[:g], [a[:g] for a in aggs], plan
+
+
+def auto_ws_bytes(q: dict) -> int:
+    return int(load().rel_groupby_auto_ws_bytes(ctypes.byref(_Desc(q).d)))
+
+
+# ---------------------------------------------------------- planner network
+
+def _f32(t: torch.Tensor, n: int | None = None) -> int:
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"expected at least {n} elements")
+    return t.data_ptr()
+
+
+def mlp_round(params: torch.Tensor, bf16: torch.Tensor, stream=None) -> None:
+    """bf16 <- round-to-nearest-even(params) (rel_mlp_round)."""
+    if bf16.dtype != torch.bfloat16 or bf16.numel() < MLP_PARAMS:
+        raise ValueError("bf16 must hold MLP_PARAMS bfloat16 values")
+    _check(load().rel_mlp_round(_f32(params, MLP_PARAMS), bf16.data_ptr(), _stream(stream)))
+
+
+def mlp_forward(bf16: torch.Tensor, params: torch.Tensor, x: torch.Tensor,
+                acts: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """y[B, 4] for x[B, 264] (rel_mlp_forward); acts[B, 128] receives the
+    hidden pre-activations when given."""
+    B = x.shape[0]
+    out = torch.empty((B, MLP_OUT), dtype=torch.float32, device=x.device)
+    _check(load().rel_mlp_forward(bf16.data_ptr(), _f32(params, MLP_PARAMS), _f32(x, B * MLP_IN),
+                                  B, out.data_ptr(),
+                                  None if acts is None else _f32(acts, B * 2 * MLP_HIDDEN),
+                                  _stream(stream)))
+    return out
+
+
+def mlp_backward(bf16: torch.Tensor, x: torch.Tensor, acts: torch.Tensor, out: torch.Tensor,
+                 t_ndv: torch.Tensor, t_var: torch.Tensor, grad: torch.Tensor,
+                 loss: torch.Tensor, ws: torch.Tensor | None = None, stream=None) -> None:
+    """grad <- d(batch-mean loss)/d(params), loss[0] <- the loss (rel_mlp_backward)."""
+    L = load()
+    B = x.shape[0]
+    need = int(L.rel_mlp_ws_bytes(B))
+    if ws is None or ws.numel() < need:
+        ws = _ws(need, x.device)
+    if t_var.dtype != torch.int32 or not t_var.is_contiguous() or t_var.numel() < B:
+        raise ValueError("t_var must be contiguous int32[B]")
+    _check(L.rel_mlp_backward(bf16.data_ptr(), _f32(x, B * MLP_IN), _f32(acts, B * 2 * MLP_HIDDEN),
+                              _f32(out, B * MLP_OUT), _f32(t_ndv, B), t_var.data_ptr(), B,
+                              ws.data_ptr(), ws.numel(), _f32(grad, MLP_PARAMS), _f32(loss, 1),
+                              _stream(stream)))
+
+
+def mlp_adamw(params: torch.Tensor, bf16: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+              grad: torch.Tensor, step: int, lr: float = 1e-3, beta1: float = 0.9,
+              beta2: float = 0.999, eps: float = 1e-8, weight_decay: float = 1e-4,
+              stream=None) -> None:
+    """One AdamW step on the parameters, refreshing the BF16 copy (rel_mlp_adamw)."""
+    _check(load().rel_mlp_adamw(_f32(params, MLP_PARAMS), bf16.data_ptr(), _f32(m, MLP_PARAMS),
+                                _f32(v, MLP_PARAMS), _f32(grad, MLP_PARAMS), step, lr, beta1,
+                                beta2, eps, weight_decay, _stream(stream)))
+
+
+_planner_ref = None  # keeps the registered parameter tensors alive
+
+
+def planner_set(params: torch.Tensor | None) -> None:
+    """Register FP32 parameters (and a BF16 copy made here) as the network
+    REL_PLAN_LEARNED consults; None clears."""
+    global _planner_ref
+    L = load()
+    if params is None:
+        _check(L.rel_planner_set(None, None))
+        _planner_ref = None
+        return
+    p = params.detach().to(torch.float32).contiguous()
+    bf = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=p.device)
+    mlp_round(p, bf)
+    torch.cuda.current_stream(p.device).synchronize()
+    _check(L.rel_planner_set(bf.data_ptr(), _f32(p, MLP_PARAMS)))
+    _planner_ref = (p, bf)
 
 
 def sketch(q: dict, stream=None) -> "SketchInfo":

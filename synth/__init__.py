@@ -194,3 +194,31 @@ def few_keys_kv(n: int, n_keys: int = 4, seed: int = 0):
     keys = uniform_mixed(n, 1, n_keys, seed, TAG_KEY)
     vals = uniform(n, -1_000_000, 1_000_000, seed, TAG_VAL)
     return keys, vals
+
+
+def mlp_params(seed: int, n_in: int = 264, n_h: int = 64, n_out: int = 4) -> np.ndarray:
+    """Random parameters of the planner network (float32, layout W1 b1 W2 b2
+    W3 b3): weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases U(-0.1, 0.1)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((n_h, n_in), (n_h, n_h), (n_out, n_h)):
+        s = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-s, s, fan_out * fan_in))
+        parts.append(rng.uniform(-0.1, 0.1, fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_features(n: int, seed: int) -> np.ndarray:
+    """n rows of sketch-like features (float32 [n, 264]): 256 register values
+    in [0, 1], then log2 rows in [10, 26], four shares in [0, 1], a run
+    length in [1, 64] and a key width in {0.5, 1}."""
+    rng = np.random.default_rng(seed)
+    x = np.empty((n, 264), dtype=np.float64)
+    x[:, :256] = rng.integers(0, 58, (n, 256)) / 57.0
+    x[:, 256] = rng.uniform(10, 26, n)
+    x[:, 257:261] = rng.uniform(0, 1, (n, 4))
+    x[:, 258] = rng.uniform(0, 64, n)
+    x[:, 261] = rng.uniform(0, 1, n)
+    x[:, 262] = rng.uniform(1, 64, n)
+    x[:, 263] = rng.choice([0.5, 1.0], n)
+    return x.astype(np.float32)

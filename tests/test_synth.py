@@ -68,3 +68,16 @@ def test_few_keys():
     k, v = synth.few_keys_kv(100_000, n_keys=4, seed=0)
     assert sorted(np.unique(k).tolist()) == sorted(synth.mix64_signed(i) for i in (1, 2, 3, 4))
     assert v.min() >= -1_000_000 and v.max() <= 1_000_000 and v.min() < -999_000
+
+
+def test_gpu_instance_recipe_ranges():
+    from synth import gpu as G
+
+    fams = set()
+    for seed in range(300):
+        inst = G.instance(seed)
+        assert 1_000_000 <= inst["rows"] <= 50_000_000
+        assert 10 <= inst["domain"] <= 100_000_000
+        fams.add(inst["family"])
+        assert G.instance(seed) == inst
+    assert fams == {f[0] for f in G.FAMILIES}
