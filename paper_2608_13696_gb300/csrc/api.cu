@@ -486,7 +486,13 @@ void choose_partitioned(int64_t est, int64_t n_rows, rel_plan* plan) {
   plan->smem_slots = (int32_t)next_pow2(keys_per_part * 5 / 2 < 256 ? 256 : keys_per_part * 5 / 2);
   if (plan->smem_slots > SHARED_MAX_SLOTS) plan->smem_slots = SHARED_MAX_SLOTS;
   plan->tiny_slots = 0;     // pinned heavy hitters only (from a sketch)
-  plan->slots = (int64_t)next_pow2((uint64_t)(est / 4 > 65536 ? est / 4 : 65536));
+  // spill table: a partition whose keys do not all fit its table sends all
+  // of them to the global table.  Sized for a quarter of the keys while the
+  // partition tables stay below 0.4 load; for every key once they cannot
+  // (more keys per partition than half a table of the largest size)
+  uint64_t spill = (uint64_t)est / 4;
+  if (2 * keys_per_part > (uint64_t)plan->smem_slots) spill = 2 * (uint64_t)est;
+  plan->slots = (int64_t)next_pow2(spill > 65536 ? spill : 65536);
   (void)n_rows;
 }
 
@@ -984,7 +990,7 @@ uint64_t rel_groupby_auto_ws_bytes(const rel_groupby_desc* d) {
   // every estimate is at most n_rows
   const uint64_t n = (uint64_t)d->n_rows;
   const uint64_t slots = next_pow2(2 * n < 16 ? 16 : 2 * n);
-  const uint64_t p_slots = next_pow2(n / 4 > 65536 ? n / 4 : 65536);
+  const uint64_t p_slots = next_pow2(2 * n > 65536 ? 2 * n : 65536);
   uint64_t need = gb_ws_bytes((int64_t)slots, d->n_aggs);
   need = std::max(need, part_layout((int64_t)p_slots, d->n_aggs, PART_MAX_BITS, d->n_rows).end);
   need = std::max(need, HEADER_BYTES + 8 * slots);  // exact pre-pass key set

@@ -140,3 +140,24 @@ def test_auto_workspace_too_small():
     r = L.rel_groupby_auto(ctypes.byref(d.d), rel.PLAN_EXACT, ws.data_ptr(), need - 256,
                            out.data_ptr(), ptrs, 16, ctypes.byref(n), None, None)
     assert r == rel.REL_E_CAPACITY and n.value == -7
+
+
+def test_forced_partitioned_many_groups():
+    # ~24M distinct keys: the partition tables cannot hold them all, so the
+    # spill table must take the rest without overflowing
+    from synth import gpu as G
+
+    n = 24_000_000
+    k, v = G.kv(0, 0.0, n, 1 << 60, seed=21)
+    qc = {"cols": [k, v], "keys": [0], "preds": [],
+          "aggs": [("sum", 1, []), ("count", 1, []), ("min", 1, []), ("max", 1, [])]}
+    keys, aggs, plan = rel.groupby_auto(qc, flags=rel.PLAN_EXACT |
+                                        rel.plan_force(rel.VAR_PARTITIONED))
+    assert plan.variant == rel.VAR_PARTITIONED
+    kn = k.cpu().numpy()
+    uk, cnt = np.unique(kn, return_counts=True)
+    assert keys.numel() == uk.size
+    gk, ga = canon_groupby(keys, aggs)
+    assert np.array_equal(gk, uk)
+    assert np.array_equal(ga[1], cnt)
+    assert int(ga[0].sum()) == int(v.sum().item())
