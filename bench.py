@@ -142,6 +142,18 @@ def algo_bytes(kernel, part, inp, res):
         return inp["bk"].nbytes + inp["bp"].nbytes
     if kernel == "join_probe":
         return inp["pk"].nbytes + res["join"][0].numel() * 16
+    # partitioned variant: histogram reads the keys; scatter reads key and
+    # value and writes a 16-byte record per row; aggregation reads the
+    # records and writes the groups
+    if part in cols:
+        n = cols[part][0].shape[0]
+        if kernel == "gb_part_hist":
+            return cols[part][0].nbytes
+        if kernel == "gb_part_scatter":
+            return sum(c.nbytes for c in cols[part]) + 16 * n
+        if kernel == "gb_part_agg":
+            k, aggs = res[part]
+            return 16 * n + k.numel() * 8 * (1 + len(aggs))
     return 0
 
 
@@ -286,6 +298,10 @@ def main():
     ap.add_argument("--small", action="store_true", help="10x smaller workload (quick checks)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--learned", type=int, default=200,
+                    help="instances of the learned-sizing comparison (0 = skip)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-plain comparison")
     args = ap.parse_args()
     sz = full_sizes(args.small)
     if args.impl == "reference":
@@ -404,11 +420,56 @@ def main():
         v, _ = extrapolate(t, rows_full)
         line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
                                 "sample": sample_text(CPU_FRACS, sz)}
+    if rank == 0 and args.learned > 0:
+        line["learned"] = run_learned(args)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = run_batched(args)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_learned(args):
+    """Learned sizing (sketch + planner network) against the plain exact
+    pre-pass, on instances of 1e6..5e7 rows (uniform, Zipf 0.5/1/1.5,
+    clustered keys) the network was not trained on; results compared."""
+    from paper_2608_13696_gb300 import planner
+
+    if not os.path.exists(planner.DEFAULT_WEIGHTS):
+        return {"skipped": "no trained planner network"}
+    n = args.learned if not args.small else min(args.learned, 20)
+    r = planner.evaluate(range(1_000_000, 1_000_000 + n), with_labels=False, log_every=0,
+                         rows_hi=50_000_000 if not args.small else 5_000_000)
+    r.pop("per_instance", None)
+    r["timing"] = "wall clock per instance (plan + run + result count), inputs resident, L2 flushed"
+    return r
+
+
+def run_batched(args):
+    """The batched workload (4096 group-bys + 512 join partitions) as one
+    graph-replayed batch against one call sequence per instance."""
+    import torch
+
+    from paper_2608_13696_gb300 import batched, planner, rel
+    from synth import gpu as G
+
+    if not os.path.exists(planner.DEFAULT_WEIGHTS):
+        return {"skipped": "no trained planner network"}
+    planner.use_default()
+    recipe = G.batch_recipe(0) if not args.small else G.batch_recipe(0, 512, 64)
+    gb, jn = G.batch_inputs(recipe)
+    torch.cuda.synchronize()
+    r = batched.measure(gb, jn, reps=3, autotune=True,
+                        candidates=[c for c in rel.BATCH_SEARCH if c[2] in (1, 2)])
+    r["config"] = list(r["config"])
+    r["workload"] = (f"{len(gb)} group-bys (rows log-U[1e3,4e6], groups log-U[1,1e5], int32/int64 "
+                     f"keys, sum+count) + {len(jn)} join partitions (build log-U[1e3,2.56e5], "
+                     f"probe log-U[8e3,2e6], 90% hits)")
+    del gb, jn
+    torch.cuda.empty_cache()
+    return r
 
 
 def run_e2e(args, g, inp, stream, world, barrier, rows_step):

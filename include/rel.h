@@ -268,6 +268,12 @@ uint64_t rel_sketch_ws_bytes(void);
 rel_status rel_sketch(const rel_groupby_desc* desc, void* ws, size_t ws_bytes,
                       rel_sketch_info* out, void* stream);
 
+/* Sketches of n inputs in one launch (one CTA each) and one read-back:
+ * out[i] as rel_sketch(descs + i).  ws: rel_sketch_batched_ws_bytes(n). */
+uint64_t rel_sketch_batched_ws_bytes(int32_t n);
+rel_status rel_sketch_batched(const rel_groupby_desc* descs, int32_t n, void* ws, size_t ws_bytes,
+                              rel_sketch_info* out, void* stream);
+
 /* Group-by without any device allocation, for callers that cannot allocate
  * device memory: an engine whose own pool owns all of the GPU's memory and
  * forbids other allocations, a plugin whose host process caps device memory,
@@ -340,6 +346,92 @@ rel_status rel_mlp_adamw(float* params, void* bf16_params, float* m, float* v, c
 /* Register the network REL_PLAN_LEARNED plans with (device pointers, kept by
  * reference; NULL clears).  Not thread-safe against concurrent planning. */
 rel_status rel_planner_set(const void* bf16_params, const float* params);
+
+/* -------------------------------------------------- batched execution */
+
+/* Many small group-bys and joins in two persistent launches (the paper's
+ * launches too small to fill the GPU, Sec. 5.3).  The caller describes every
+ * instance, rel_batch_prepare writes the descriptors into the workspace and
+ * fills a host handle, and rel_batch_run issues the device work only (one
+ * memset, two launches, no host synchronisation, no allocation), so a CUDA
+ * graph can capture it and replay it while the inputs stay where they are.
+ * Results equal those of rel_groupby_agg / rel_join_probe instance by
+ * instance (same groups and pairs; order unspecified).  The paper has no
+ * batched form; this is an execution mode of this library. */
+
+#define REL_BATCH_MAX_AGGS 4
+
+/* A key/value group-by: one int32 or int64 key column, aggregates of one
+ * int64 value column. */
+typedef struct {
+  const void* keys;        /* device, n_rows keys */
+  const int64_t* vals;     /* device, n_rows values; NULL if every op is COUNT */
+  int64_t n_rows;
+  int32_t key_type;        /* REL_I32 or REL_I64 */
+  int32_t n_aggs;          /* 1..4 */
+  int32_t ops[REL_BATCH_MAX_AGGS]; /* REL_SUM / REL_COUNT / REL_MIN / REL_MAX */
+  int64_t slots;           /* global table slots, power of two >= 16, >= the groups */
+  int64_t est_groups;      /* expected groups: decides shared-memory pre-aggregation */
+  int64_t* out_keys;       /* device, out_capacity entries */
+  int64_t* out_aggs[REL_BATCH_MAX_AGGS];
+  int64_t out_capacity;
+} rel_batch_groupby;
+
+/* A join partition: build side (unique or not), probe side, outputs. */
+typedef struct {
+  const int64_t* build_keys;
+  const int64_t* build_payload;
+  int64_t n_build;         /* < 2^31 */
+  const int64_t* probe_keys;
+  int64_t n_probe;         /* < 2^31 */
+  int32_t* out_probe_idx;
+  int32_t* out_build_idx;
+  int64_t* out_payload;
+  int64_t out_capacity;
+} rel_batch_join;
+
+typedef struct {
+  int32_t block;           /* threads per CTA: 128, 256 or 512 */
+  int32_t items;           /* rows per thread per tile: 4, 8 or 16 */
+  int32_t probe_width;     /* threads probing the global table together: 1, 2, 4, 8 */
+  int32_t smem_max_groups; /* group-bys with est_groups <= this (at most 512)
+                              pre-aggregate each tile in shared memory; 0 = none */
+} rel_batch_config;
+
+/* Host handle filled by rel_batch_prepare (opaque, caller-owned). */
+typedef struct {
+  uint64_t words[40];
+} rel_batch_handle;
+
+/* Device bytes the batch needs (descriptors, counters, every table). */
+uint64_t rel_batch_ws_bytes(const rel_batch_groupby* gb, int32_t n_gb, const rel_batch_join* jn,
+                            int32_t n_jn);
+
+/* Validate, lay out and upload the batch (synchronises the stream once).
+ * REL_E_INVALID for a bad instance or config, REL_E_UNSUPPORTED beyond a
+ * limit, REL_E_CAPACITY when ws is too small. */
+rel_status rel_batch_prepare(const rel_batch_groupby* gb, int32_t n_gb, const rel_batch_join* jn,
+                             int32_t n_jn, const rel_batch_config* cfg, void* ws, size_t ws_bytes,
+                             rel_batch_handle* handle, void* stream);
+
+/* Zero the batch's tables and counters and run both launches on stream. */
+rel_status rel_batch_run(const rel_batch_handle* handle, void* stream);
+
+/* After a run: per instance (group-bys first, then joins) the number of
+ * groups / pairs (even when larger than out_capacity) and a flag word: bit 0
+ * table overflow (re-plan that instance larger), bit 1 output capacity
+ * exceeded.  Synchronises the stream. */
+rel_status rel_batch_results(const rel_batch_handle* handle, int64_t* n_out, uint32_t* flags,
+                             void* stream);
+
+/* Time each candidate config (one warm-up run, then `reps` runs, median) and
+ * leave the fastest prepared in *handle and copied to *best; ms (host,
+ * n_cands floats, may be NULL) receives every candidate's time, or -1 for a
+ * candidate that failed validation. */
+rel_status rel_batch_autotune(const rel_batch_groupby* gb, int32_t n_gb, const rel_batch_join* jn,
+                              int32_t n_jn, const rel_batch_config* cands, int32_t n_cands,
+                              int32_t reps, void* ws, size_t ws_bytes, rel_batch_handle* handle,
+                              rel_batch_config* best, float* ms, void* stream);
 
 /* ----------------------------------------------------------------- join */
 

@@ -1,0 +1,197 @@
+"""The batched workload: thousands of uneven key/value group-bys and join
+partitions, run (a) as one batch -- sizes from the learned planner (one
+sketch launch and one network launch for all instances), then one memset and
+two persistent launches replayed from a CUDA graph, with the autotuned tile
+shape -- and (b) the plain way, one call sequence per instance (exact
+pre-pass + aggregation per group-by; build, count and probe per join).
+
+Both forms give the same groups and pairs; `compare` checks that instance by
+instance.  Instances whose learned table overflowed are re-run exactly on
+their own (the planner's fallback).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import rel
+
+GB_OPS = ["sum", "count"]
+
+
+def kv_query(keys: torch.Tensor, vals: torch.Tensor, ops=GB_OPS) -> dict:
+    return {"cols": [keys, vals], "keys": [0], "preds": [], "aggs": [(op, 1, []) for op in ops]}
+
+
+def next_pow2(x: int) -> int:
+    p = 1
+    while p < x:
+        p <<= 1
+    return p
+
+
+def learned_sizes(gb_inputs, planner_params: torch.Tensor | None = None):
+    """Per group-by (est_groups, slots, variant) from the batched sketch and
+    one batched network forward (the registered planner's parameters)."""
+    if not gb_inputs:
+        return []
+    qs = [kv_query(k, v) for k, v in gb_inputs]
+    infos = rel.sketch_batched(qs)
+    dev = gb_inputs[0][0].device
+    x = torch.from_numpy(np.stack([np.frombuffer(bytes(s.features), dtype=np.float32)
+                                   for s in infos])).to(dev)
+    p = planner_params if planner_params is not None else rel._planner_ref[0]
+    bf = torch.empty(rel.MLP_PARAMS, dtype=torch.bfloat16, device=dev)
+    rel.mlp_round(p, bf)
+    y = rel.mlp_forward(bf, p, x).cpu().numpy()
+    out = []
+    for (k, _), s, yi in zip(gb_inputs, infos, y):
+        n = k.numel()
+        est = n
+        if math.isfinite(yi[0]):
+            est = min(n, math.ceil(2.0 ** min(max(float(yi[0]), 0.0), 62.0) * 1.25))
+        est = max(est, int(s.ndv))
+        variant = 1 + int(np.argmax(yi[1:3]))  # per-CTA tables or global table
+        out.append((est, next_pow2(max(16, 2 * est)), variant))
+    return out
+
+
+def make_batch(gb_inputs, join_inputs, sizes) -> rel.Batch:
+    gs = []
+    for (k, v), (est, slots, variant) in zip(gb_inputs, sizes):
+        # est drives shared-memory placement; a network that prefers the
+        # global table gets none
+        gs.append({"keys": k, "vals": v, "ops": GB_OPS, "slots": slots,
+                   "est_groups": est if variant == rel.VAR_SMEM else 1 << 40,
+                   "capacity": max(1, min(k.numel(), slots))})
+    js = [{"build_keys": bk, "build_payload": bp, "probe_keys": pk,
+           "capacity": max(1, pk.numel())} for bk, bp, pk in join_inputs]
+    return rel.Batch(gs, js)
+
+
+def fallback(batch: rel.Batch, counts, flags):
+    """Re-run, one by one, the instances the batch could not finish: a table
+    overflow (group-by: exact re-plan) or an output larger than its capacity.
+    Returns {index: outputs}."""
+    ng = len(batch.gspec)
+    redo = {}
+    for i, f in enumerate(flags):
+        if not f:
+            continue
+        if i < ng:
+            q = batch.gspec[i]
+            keys, aggs, _ = rel.groupby_auto(kv_query(q["keys"], q["vals"]), flags=rel.PLAN_EXACT)
+            redo[i] = (keys, aggs)
+        else:
+            q = batch.jspec[i - ng]
+            t = rel.JoinTable(q["build_keys"], q["build_payload"])
+            redo[i] = t.probe(q["probe_keys"], capacity=max(1, t.count(q["probe_keys"])))
+    return redo
+
+
+def run_plain(gb_inputs, join_inputs):
+    """One call sequence per instance; returns the outputs in order."""
+    out = []
+    for k, v in gb_inputs:
+        keys, aggs, _ = rel.groupby_auto(kv_query(k, v), flags=rel.PLAN_EXACT, capacity=None)
+        out.append((keys, aggs))
+    for bk, bp, pk in join_inputs:
+        t = rel.JoinTable(bk, bp)
+        n = t.count(pk)
+        out.append(t.probe(pk, capacity=max(1, n)))
+    return out
+
+
+def _same_groups(a, b) -> bool:
+    (ka, aa), (kb, ab) = a, b
+    if ka.numel() != kb.numel():
+        return False
+    sa, oa = torch.sort(ka)
+    sb, ob = torch.sort(kb)
+    return torch.equal(sa, sb) and all(torch.equal(x[oa], y[ob]) for x, y in zip(aa, ab))
+
+
+def _same_pairs(a, b) -> bool:
+    pa, ba, ya = a
+    pb, bb, yb = b
+    if pa.numel() != pb.numel():
+        return False
+    ka = pa.to(torch.int64) * (1 << 32) + ba.to(torch.int64)
+    kb = pb.to(torch.int64) * (1 << 32) + bb.to(torch.int64)
+    sa, oa = torch.sort(ka)
+    sb, ob = torch.sort(kb)
+    return torch.equal(sa, sb) and torch.equal(ya[oa], yb[ob])
+
+
+def batch_outputs(batch: rel.Batch, counts, redo):
+    ng = len(batch.gspec)
+    out = []
+    for i in range(ng + len(batch.jspec)):
+        if i in redo:
+            out.append(redo[i])
+        elif i < ng:
+            out.append(batch.groupby_output(i, counts[i]))
+        else:
+            out.append(batch.join_output(i - ng, counts[i]))
+    return out
+
+
+def compare(batched_out, plain_out, n_groupby: int) -> int:
+    """Number of instances whose results differ."""
+    bad = 0
+    for i, (a, b) in enumerate(zip(batched_out, plain_out)):
+        same = _same_groups(a, b) if i < n_groupby else _same_pairs(a, b)
+        bad += not same
+    return bad
+
+
+def measure(gb_inputs, join_inputs, reps: int = 3, autotune: bool = True,
+            candidates=None, planner_params=None) -> dict:
+    """Wall time of both forms (inputs resident), results compared."""
+    sync = torch.cuda.synchronize
+    rows = sum(k.numel() for k, _ in gb_inputs) + sum(pk.numel() for _, _, pk in join_inputs)
+    # batched: plan (sketch + network), prepare (+ autotune), graph, replay
+    sync()
+    t0 = time.perf_counter()
+    sizes = learned_sizes(gb_inputs, planner_params)
+    b = make_batch(gb_inputs, join_inputs, sizes)
+    sync()
+    t_plan = time.perf_counter() - t0
+    tuned = None
+    if autotune:
+        tuned, _ = b.autotune(candidates)
+    else:
+        b.prepare()
+    g = b.capture()
+    times = []
+    for _ in range(reps):
+        sync()
+        t0 = time.perf_counter()
+        g.replay()
+        counts, flags = b.results()
+        redo = fallback(b, counts, flags)
+        sync()
+        times.append(time.perf_counter() - t0)
+    t_batch = float(np.median(times))
+    batched_out = batch_outputs(b, counts, redo)
+    # plain
+    times = []
+    plain_out = None
+    for _ in range(reps):
+        sync()
+        t0 = time.perf_counter()
+        plain_out = run_plain(gb_inputs, join_inputs)
+        sync()
+        times.append(time.perf_counter() - t0)
+    t_plain = float(np.median(times))
+    mismatches = compare(batched_out, plain_out, len(gb_inputs))
+    return {"instances": len(gb_inputs) + len(join_inputs), "rows": rows,
+            "batched_s": t_batch, "plan_s": t_plan, "plain_s": t_plain,
+            "batched_rows_per_s": rows / t_batch,
+            "batched_with_plan_rows_per_s": rows / (t_batch + t_plan),
+            "plain_rows_per_s": rows / t_plain, "speedup": t_plain / t_batch,
+            "speedup_with_plan": t_plain / (t_batch + t_plan),
+            "fallbacks": len(redo), "mismatches": mismatches, "config": tuned or b.config}

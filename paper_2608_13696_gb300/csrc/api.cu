@@ -626,6 +626,68 @@ rel_status set_layers(GbParams& p, const rel_plan* plan, int shape) {
   return REL_OK;
 }
 
+// Kernel parameters of a sketch; returns the key width in bits.
+int sketch_params(const rel_groupby_desc* d, SketchParams* sp) {
+  std::memset(sp, 0, sizeof *sp);
+  sp->n_rows = d->n_rows;
+  for (int c = 0; c < d->n_cols; ++c) {
+    sp->col[c] = (const uint8_t*)d->cols[c].data;
+    sp->ctype[c] = d->cols[c].type;
+  }
+  sp->n_keys = d->n_keys;
+  sp->n_preds = d->n_preds;
+  int shift = 0, bits = 0;
+  for (int k = d->n_keys - 1; k >= 0; --k) {
+    const int w = elem_bits(d->cols[d->key_cols[k]].type);
+    sp->key_col[k] = d->key_cols[k];
+    sp->key_shift[k] = d->n_keys == 1 ? 0 : shift;
+    sp->key_mask[k] = w >= 64 ? ~0ull : ((1ull << w) - 1);
+    shift += w;
+    bits += w;
+  }
+  for (int i = 0; i < d->n_preds; ++i) {
+    sp->pred_col[i] = d->preds[i].col;
+    sp->pred_lo[i] = d->preds[i].lo;
+    sp->pred_hi[i] = d->preds[i].hi;
+  }
+  return bits;
+}
+
+// The host summary and the 264 features of a device sketch.
+void sketch_fill(const rel_groupby_desc* d, const DevSketch& h, int bits, rel_sketch_info* out) {
+  std::memset(out, 0, sizeof *out);
+  out->n_rows = d->n_rows;
+  out->sample_rows = h.sample_rows;
+  out->kept = h.kept;
+  out->ndv = h.ndv;
+  out->singletons = h.singletons;
+  out->runs = h.runs;
+  out->key_bits = bits;
+  out->key_min = h.key_min;
+  out->key_max = h.key_max;
+  for (int i = 0; i < REL_SKETCH_TOP; ++i) {
+    out->top_key[i] = h.top_key[i];
+    out->top_count[i] = h.top_count[i];
+  }
+  for (int i = 0; i < 256; ++i) {
+    out->hll[i] = h.hll[i];
+    out->features[i] = (float)(h.hll[i] / 57.0);
+  }
+  const double kept = h.kept, ndv = h.ndv;
+  double top8 = 0;
+  for (int i = 0; i < 8; ++i) top8 += h.top_count[i];
+  float* f = out->features + 256;
+  f[0] = (float)std::log2(d->n_rows > 1 ? (double)d->n_rows : 1.0);
+  f[1] = (float)(h.kept ? ndv / kept : 0.0);
+  f[2] = (float)(h.kept ? std::log2((double)((uint64_t)h.key_max - (uint64_t)h.key_min) + 1.0)
+                        : 0.0);
+  f[3] = (float)(h.kept ? h.top_count[0] / kept : 0.0);
+  f[4] = (float)(h.kept ? top8 / kept : 0.0);
+  f[5] = (float)(h.ndv ? h.singletons / ndv : 0.0);
+  f[6] = (float)(h.runs ? kept / h.runs : 0.0);
+  f[7] = (float)(bits / 64.0);
+}
+
 // The network REL_PLAN_LEARNED consults (caller-owned device memory).
 const void* g_planner_bf16 = nullptr;
 const float* g_planner_f32 = nullptr;
@@ -906,7 +968,7 @@ const char* rel_kernel_name(int32_t id) {
   static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
                                 "join_build", "join_probe", "join_count", "sketch", "gb_main_regs",
                                 "gb_part_hist", "gb_part_scan", "gb_part_scatter",
-                                "gb_part_agg", "mlp"};
+                                "gb_part_agg", "mlp", "batch_a", "batch_b"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 
@@ -1034,28 +1096,7 @@ rel_status rel_sketch(const rel_groupby_desc* d, void* ws, size_t ws_bytes, rel_
                      (unsigned long long)rel_sketch_ws_bytes()),
            REL_E_CAPACITY;
   SketchParams sp;
-  std::memset(&sp, 0, sizeof sp);
-  sp.n_rows = d->n_rows;
-  for (int c = 0; c < d->n_cols; ++c) {
-    sp.col[c] = (const uint8_t*)d->cols[c].data;
-    sp.ctype[c] = d->cols[c].type;
-  }
-  sp.n_keys = d->n_keys;
-  sp.n_preds = d->n_preds;
-  int shift = 0, bits = 0;
-  for (int k = d->n_keys - 1; k >= 0; --k) {
-    const int w = elem_bits(d->cols[d->key_cols[k]].type);
-    sp.key_col[k] = d->key_cols[k];
-    sp.key_shift[k] = d->n_keys == 1 ? 0 : shift;
-    sp.key_mask[k] = w >= 64 ? ~0ull : ((1ull << w) - 1);
-    shift += w;
-    bits += w;
-  }
-  for (int i = 0; i < d->n_preds; ++i) {
-    sp.pred_col[i] = d->preds[i].col;
-    sp.pred_lo[i] = d->preds[i].lo;
-    sp.pred_hi[i] = d->preds[i].hi;
-  }
+  const int bits = sketch_params(d, &sp);
   cudaStream_t st = as_stream(stream);
   DevSketch* dev = (DevSketch*)ws;
   if ((r = sketch_launch(sp, dev, st))) return r;
@@ -1063,37 +1104,43 @@ rel_status rel_sketch(const rel_groupby_desc* d, void* ws, size_t ws_bytes, rel_
   cudaError_t e = cudaMemcpyAsync(&h, dev, sizeof h, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the sketch");
-  std::memset(out, 0, sizeof *out);
-  out->n_rows = d->n_rows;
-  out->sample_rows = h.sample_rows;
-  out->kept = h.kept;
-  out->ndv = h.ndv;
-  out->singletons = h.singletons;
-  out->runs = h.runs;
-  out->key_bits = bits;
-  out->key_min = h.key_min;
-  out->key_max = h.key_max;
-  for (int i = 0; i < REL_SKETCH_TOP; ++i) {
-    out->top_key[i] = h.top_key[i];
-    out->top_count[i] = h.top_count[i];
-  }
-  for (int i = 0; i < 256; ++i) {
-    out->hll[i] = h.hll[i];
-    out->features[i] = (float)(h.hll[i] / 57.0);
-  }
-  const double kept = h.kept, ndv = h.ndv;
-  double top8 = 0;
-  for (int i = 0; i < 8; ++i) top8 += h.top_count[i];
-  float* f = out->features + 256;
-  f[0] = (float)std::log2(d->n_rows > 1 ? (double)d->n_rows : 1.0);
-  f[1] = (float)(h.kept ? ndv / kept : 0.0);
-  f[2] = (float)(h.kept ? std::log2((double)((uint64_t)h.key_max - (uint64_t)h.key_min) + 1.0)
-                        : 0.0);
-  f[3] = (float)(h.kept ? h.top_count[0] / kept : 0.0);
-  f[4] = (float)(h.kept ? top8 / kept : 0.0);
-  f[5] = (float)(h.ndv ? h.singletons / ndv : 0.0);
-  f[6] = (float)(h.runs ? kept / h.runs : 0.0);
-  f[7] = (float)(bits / 64.0);
+  sketch_fill(d, h, bits, out);
+  return REL_OK;
+}
+
+uint64_t rel_sketch_batched_ws_bytes(int32_t n) {
+  if (n < 0) return 0;
+  return align_up(sizeof(SketchParams) * (uint64_t)n, 256) +
+         align_up(sizeof(DevSketch) * (uint64_t)n, 256) + 256;
+}
+
+rel_status rel_sketch_batched(const rel_groupby_desc* descs, int32_t n, void* ws, size_t ws_bytes,
+                              rel_sketch_info* out, void* stream) {
+  if (n < 0 || (n > 0 && (!descs || !out)))
+    return set_error("sketch: bad arguments"), REL_E_INVALID;
+  if (n == 0) return REL_OK;
+  rel_status r;
+  for (int i = 0; i < n; ++i)
+    if ((r = validate_desc(descs + i))) return r;
+  if (!ws || ws_bytes < rel_sketch_batched_ws_bytes(n))
+    return set_error("sketch: workspace needs %llu bytes",
+                     (unsigned long long)rel_sketch_batched_ws_bytes(n)),
+           REL_E_CAPACITY;
+  std::vector<SketchParams> sp(n);
+  std::vector<int> bits(n);
+  for (int i = 0; i < n; ++i) bits[i] = sketch_params(descs + i, &sp[i]);
+  uint8_t* base = (uint8_t*)align_up((uint64_t)(uintptr_t)ws, 256);
+  SketchParams* dp = (SketchParams*)base;
+  DevSketch* ds = (DevSketch*)(base + align_up(sizeof(SketchParams) * (uint64_t)n, 256));
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(dp, sp.data(), sizeof(SketchParams) * n, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemcpyAsync");
+  if ((r = sketch_many_launch(dp, ds, n, st))) return r;
+  std::vector<DevSketch> h(n);
+  e = cudaMemcpyAsync(h.data(), ds, sizeof(DevSketch) * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the sketches");
+  for (int i = 0; i < n; ++i) sketch_fill(descs + i, h[i], bits[i], out + i);
   return REL_OK;
 }
 

@@ -166,6 +166,8 @@ struct alignas(128) WsHeader {
   unsigned int timeout;         // a bounded wait gave up
   unsigned long long aux;       // spare counter (distinct keys in the exact pre-pass)
   unsigned long long side_aggs[REL_MAX_AGGS];
+  unsigned int dups;            // join build: some key occurs twice
+  unsigned int pad;
 };
 static_assert(sizeof(WsHeader) <= 256, "header fits in 256 bytes");
 constexpr uint64_t HEADER_BYTES = 256;
@@ -197,7 +199,9 @@ enum KernelId : int {
   K_GB_PSCATTER = 10,
   K_GB_PAGG = 11,
   K_MLP = 12,
-  K_COUNT_IDS = 13
+  K_BATCH_A = 13,
+  K_BATCH_B = 14,
+  K_COUNT_IDS = 15
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

@@ -60,8 +60,8 @@ __device__ void bitonic(int64_t* a, int64_t* b, Less less) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(SK_THREADS) sketch_k(const __grid_constant__ SketchParams p,
-                                                        DevSketch* out) {
+// One CTA sketches one input.
+__device__ __forceinline__ void sketch_body(const SketchParams& p, DevSketch* out) {
   extern __shared__ int64_t sk_dyn[];
   int64_t* key = sk_dyn;        // [SK_N] sampled keys, then sorted
   int64_t* aux = sk_dyn + SK_N;  // [SK_N] 0 kept / 1 dropped, then counts
@@ -165,7 +165,31 @@ __global__ void __launch_bounds__(SK_THREADS) sketch_k(const __grid_constant__ S
   }
 }
 
+__global__ void __launch_bounds__(SK_THREADS) sketch_k(const __grid_constant__ SketchParams p,
+                                                        DevSketch* out) {
+  sketch_body(p, out);
+}
+
+// Many inputs in one launch: CTA b sketches input b.
+__global__ void __launch_bounds__(SK_THREADS) sketch_many_k(const SketchParams* __restrict__ ps,
+                                                             DevSketch* outs) {
+  sketch_body(ps[blockIdx.x], outs + blockIdx.x);
+}
+
 }  // namespace
+
+rel_status sketch_many_launch(const SketchParams* ps, DevSketch* outs, int n, cudaStream_t st) {
+  if (n <= 0) return REL_OK;
+  const int smem = 2 * SK_N * (int)sizeof(int64_t);
+  cudaError_t e0 =
+      cudaFuncSetAttribute(sketch_many_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e0 != cudaSuccess) return relhost::cuda_fail(e0, "cudaFuncSetAttribute(sketch)");
+  relhost::launch_begin(relhost::K_SKETCH, st);
+  sketch_many_k<<<n, SK_THREADS, smem, st>>>(ps, outs);
+  relhost::launch_end(relhost::K_SKETCH, st);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(sketch, batched)");
+}
 
 rel_status sketch_launch(const SketchParams& p, DevSketch* out, cudaStream_t st) {
   const int smem = 2 * SK_N * (int)sizeof(int64_t);

@@ -31,5 +31,7 @@ struct DevSketch {
 };
 
 rel_status sketch_launch(const SketchParams& p, DevSketch* out, cudaStream_t st);
+// ps and outs: n entries in device memory.
+rel_status sketch_many_launch(const SketchParams* ps, DevSketch* outs, int n, cudaStream_t st);
 
 }  // namespace rel

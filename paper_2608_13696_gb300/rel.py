@@ -120,6 +120,37 @@ class JoinProbeDesc(ctypes.Structure):
                 ("n_probe", ctypes.c_int64)]
 
 
+BATCH_MAX_AGGS = 4
+
+
+class BatchGroupBy(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("n_rows", ctypes.c_int64),
+                ("key_type", ctypes.c_int32), ("n_aggs", ctypes.c_int32),
+                ("ops", ctypes.c_int32 * BATCH_MAX_AGGS), ("slots", ctypes.c_int64),
+                ("est_groups", ctypes.c_int64), ("out_keys", ctypes.c_void_p),
+                ("out_aggs", ctypes.c_void_p * BATCH_MAX_AGGS), ("out_capacity", ctypes.c_int64)]
+
+
+class BatchJoinC(ctypes.Structure):
+    _fields_ = [("build_keys", ctypes.c_void_p), ("build_payload", ctypes.c_void_p),
+                ("n_build", ctypes.c_int64), ("probe_keys", ctypes.c_void_p),
+                ("n_probe", ctypes.c_int64), ("out_probe_idx", ctypes.c_void_p),
+                ("out_build_idx", ctypes.c_void_p), ("out_payload", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_int64)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("items", ctypes.c_int32),
+                ("probe_width", ctypes.c_int32), ("smem_max_groups", ctypes.c_int32)]
+
+    def astuple(self):
+        return (self.block, self.items, self.probe_width, self.smem_max_groups)
+
+
+class BatchHandle(ctypes.Structure):
+    _fields_ = [("words", ctypes.c_uint64 * 40)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -129,7 +160,9 @@ EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join
            "rel_version", "rel_profile_start", "rel_profile_stop", "rel_kernel_name",
            "rel_groupby_agg_static", "rel_sketch", "rel_sketch_ws_bytes", "rel_plan_ws_bytes",
            "rel_groupby_auto", "rel_groupby_auto_ws_bytes", "rel_mlp_round", "rel_mlp_forward",
-           "rel_mlp_ws_bytes", "rel_mlp_backward", "rel_mlp_adamw", "rel_planner_set"]
+           "rel_mlp_ws_bytes", "rel_mlp_backward", "rel_mlp_adamw", "rel_planner_set",
+           "rel_batch_ws_bytes", "rel_batch_prepare", "rel_batch_run", "rel_batch_results",
+           "rel_batch_autotune", "rel_sketch_batched", "rel_sketch_batched_ws_bytes"]
 SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
 
@@ -209,6 +242,24 @@ def load(build_if_stale: bool = True):
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
         L.rel_planner_set.restype = i32
         L.rel_planner_set.argtypes = [vp, vp]
+        L.rel_sketch_batched_ws_bytes.restype = u64
+        L.rel_sketch_batched_ws_bytes.argtypes = [i32]
+        L.rel_sketch_batched.restype = i32
+        L.rel_sketch_batched.argtypes = [ctypes.POINTER(GroupByDesc), i32, vp, ctypes.c_size_t,
+                                         ctypes.POINTER(SketchInfo), vp]
+        PG, PJ = ctypes.POINTER(BatchGroupBy), ctypes.POINTER(BatchJoinC)
+        PC, PH = ctypes.POINTER(BatchConfig), ctypes.POINTER(BatchHandle)
+        L.rel_batch_ws_bytes.restype = u64
+        L.rel_batch_ws_bytes.argtypes = [PG, i32, PJ, i32]
+        L.rel_batch_prepare.restype = i32
+        L.rel_batch_prepare.argtypes = [PG, i32, PJ, i32, PC, vp, ctypes.c_size_t, PH, vp]
+        L.rel_batch_run.restype = i32
+        L.rel_batch_run.argtypes = [PH, vp]
+        L.rel_batch_results.restype = i32
+        L.rel_batch_results.argtypes = [PH, ctypes.POINTER(i64), ctypes.POINTER(u32), vp]
+        L.rel_batch_autotune.restype = i32
+        L.rel_batch_autotune.argtypes = [PG, i32, PJ, i32, PC, i32, i32, vp, ctypes.c_size_t, PH,
+                                         PC, ctypes.POINTER(ctypes.c_float), vp]
         _lib = L
         return L
 
@@ -460,6 +511,19 @@ def sketch(q: dict, stream=None) -> "SketchInfo":
     return out
 
 
+def sketch_batched(qs: list, stream=None) -> list:
+    """rel_sketch_batched: the sample summaries of many inputs, one launch."""
+    L = load()
+    if not qs:
+        return []
+    ds = [_Desc(q) for q in qs]
+    arr = (GroupByDesc * len(ds))(*[d.d for d in ds])
+    ws = _ws(L.rel_sketch_batched_ws_bytes(len(ds)), qs[0]["cols"][0].device)
+    out = (SketchInfo * len(ds))()
+    _check(L.rel_sketch_batched(arr, len(ds), ws.data_ptr(), ws.numel(), out, _stream(stream)))
+    return list(out)
+
+
 class JoinTable:
     """A built join table; owns its workspace tensor."""
 
@@ -503,3 +567,130 @@ class JoinTable:
                 continue
             _check(r)
             return pi[:n.value], bi[:n.value], pay[:n.value]
+
+
+# ------------------------------------------------------- batched execution
+
+DEFAULT_BATCH_CONFIG = (256, 8, 1, 512)
+# the tuner's search space: block x items x probe width x shared-memory placement
+BATCH_SEARCH = [(b, it, w, sm) for b in (128, 256, 512) for it in (4, 8, 16)
+                for w in (1, 2, 4, 8) for sm in (0, 512)]
+
+
+class Batch:
+    """Many key/value group-bys and join partitions run as one batch
+    (rel_batch_*): two persistent launches, replayable from a CUDA graph.
+
+    groupbys: dicts with keys (int32/int64 CUDA tensor), vals (int64 or None),
+      ops (list of "sum"/"count"/"min"/"max"), slots (power of two), est_groups,
+      capacity (output rows).
+    joins: dicts with build_keys, build_payload, probe_keys (int64), capacity.
+    Outputs are allocated here; inputs must stay alive and in place."""
+
+    def __init__(self, groupbys, joins, device=None, stream=None):
+        L = load()
+        self.gspec, self.jspec = list(groupbys), list(joins)
+        dev = device or (self.gspec[0]["keys"].device if self.gspec
+                         else self.jspec[0]["build_keys"].device if self.jspec else "cuda")
+        self.device = torch.device(dev)
+        ng, nj = len(self.gspec), len(self.jspec)
+        self.g = (BatchGroupBy * max(1, ng))()
+        self.j = (BatchJoinC * max(1, nj))()
+        self.gout, self.jout = [], []
+        for i, q in enumerate(self.gspec):
+            k, v = q["keys"], q.get("vals")
+            if k.dtype not in (torch.int32, torch.int64) or not k.is_contiguous():
+                raise ValueError("group-by keys must be contiguous int32/int64")
+            if v is not None and (v.dtype != torch.int64 or v.numel() != k.numel()):
+                raise ValueError("group-by values must be int64 of the keys' length")
+            ops = q["ops"]
+            cap = max(1, int(q["capacity"]))
+            ok = torch.empty(cap, dtype=torch.int64, device=self.device)
+            oa = [torch.empty(cap, dtype=torch.int64, device=self.device) for _ in ops]
+            self.gout.append((ok, oa))
+            d = self.g[i]
+            d.keys, d.vals, d.n_rows = k.data_ptr(), (v.data_ptr() if v is not None else None), k.numel()
+            d.key_type = _DT[k.dtype]
+            d.n_aggs = len(ops)
+            for a, op in enumerate(ops):
+                d.ops[a] = OPS[op]
+                d.out_aggs[a] = oa[a].data_ptr()
+            d.slots, d.est_groups = int(q["slots"]), int(q.get("est_groups", 0))
+            d.out_keys, d.out_capacity = ok.data_ptr(), cap
+        for i, q in enumerate(self.jspec):
+            bk, bp, pk = q["build_keys"], q["build_payload"], q["probe_keys"]
+            for t in (bk, bp, pk):
+                if t.dtype != torch.int64 or not t.is_contiguous():
+                    raise ValueError("join columns must be contiguous int64")
+            cap = max(1, int(q["capacity"]))
+            o = (torch.empty(cap, dtype=torch.int32, device=self.device),
+                 torch.empty(cap, dtype=torch.int32, device=self.device),
+                 torch.empty(cap, dtype=torch.int64, device=self.device))
+            self.jout.append(o)
+            d = self.j[i]
+            d.build_keys, d.build_payload, d.n_build = bk.data_ptr(), bp.data_ptr(), bk.numel()
+            d.probe_keys, d.n_probe = pk.data_ptr(), pk.numel()
+            d.out_probe_idx, d.out_build_idx, d.out_payload = (x.data_ptr() for x in o)
+            d.out_capacity = cap
+        need = int(L.rel_batch_ws_bytes(self.g, ng, self.j, nj))
+        if need == 0 and (ng or nj):
+            raise RelError(REL_E_INVALID, "invalid batch")
+        self.ws = _ws(need, self.device)
+        self.h = BatchHandle()
+        self.config = None
+
+    def prepare(self, config=DEFAULT_BATCH_CONFIG, stream=None):
+        c = BatchConfig(*config)
+        _check(load().rel_batch_prepare(self.g, len(self.gspec), self.j, len(self.jspec),
+                                        ctypes.byref(c), self.ws.data_ptr(), self.ws.numel(),
+                                        ctypes.byref(self.h), _stream(stream)))
+        self.config = tuple(config)
+        return self
+
+    def autotune(self, candidates=None, reps: int = 3, stream=None):
+        """Time every candidate (block, items, probe width, smem_max_groups);
+        keeps the fastest prepared.  Returns (best, {config: ms})."""
+        cands = list(candidates or BATCH_SEARCH)
+        arr = (BatchConfig * len(cands))(*[BatchConfig(*c) for c in cands])
+        best = BatchConfig()
+        ms = (ctypes.c_float * len(cands))()
+        _check(load().rel_batch_autotune(self.g, len(self.gspec), self.j, len(self.jspec), arr,
+                                         len(cands), reps, self.ws.data_ptr(), self.ws.numel(),
+                                         ctypes.byref(self.h), ctypes.byref(best), ms,
+                                         _stream(stream)))
+        self.config = best.astuple()
+        return self.config, {c: float(ms[i]) for i, c in enumerate(cands)}
+
+    def run(self, stream=None):
+        _check(load().rel_batch_run(ctypes.byref(self.h), _stream(stream)))
+
+    def capture(self):
+        """A CUDA graph of one run (prepare first); replay() reruns the batch."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            self.run(stream=s)  # warm-up outside the graph
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        return g
+
+    def results(self, stream=None):
+        """(counts int64[n_g + n_j], flags uint32[n_g + n_j]); flag bit 0 =
+        table overflow, bit 1 = output capacity exceeded."""
+        n = len(self.gspec) + len(self.jspec)
+        cnt = (ctypes.c_int64 * max(1, n))()
+        fl = (ctypes.c_uint32 * max(1, n))()
+        _check(load().rel_batch_results(ctypes.byref(self.h), cnt, fl, _stream(stream)))
+        return [int(cnt[i]) for i in range(n)], [int(fl[i]) for i in range(n)]
+
+    def groupby_output(self, i: int, n: int):
+        k, a = self.gout[i]
+        n = min(n, k.numel())
+        return k[:n], [x[:n] for x in a]
+
+    def join_output(self, i: int, n: int):
+        pi, bi, pay = self.jout[i]
+        n = min(n, pi.numel())
+        return pi[:n], bi[:n], pay[:n]

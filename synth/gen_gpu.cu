@@ -19,9 +19,15 @@
  *                cut after 4096 rows), the run's rank = U[1, D] drawn at its
  *                first row.
  * Values: U[-10^6, 10^6].
+ *
+ * Join sides: the build and probe streams of gen.c (40-bit Feistel
+ * permutation keys, Bernoulli hits), bit-identical to syn_join_build and
+ * syn_join_probe.
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <climits>
 
 namespace {
 
@@ -100,7 +106,77 @@ __global__ void kv_kernel(int family, double s, int64_t n, int64_t domain, uint6
   }
 }
 
+// The join streams of gen.c, row for row (see syn_join_build / syn_join_probe).
+constexpr uint64_t TAG_PERM = 0x50, TAG_PAYLOAD = 0x51, TAG_HIT = 0x52, TAG_PICK = 0x53,
+                   TAG_MISS = 0x54;
+
+__device__ inline uint64_t perm40(uint64_t x, uint64_t pkey) {
+  const uint64_t M = (1ull << 20) - 1;
+  uint64_t L = (x >> 20) & M, R = x & M;
+  for (uint64_t k = 0; k < 4; k++) {
+    const uint64_t rk = mix64(pkey ^ (k + 1));
+    const uint64_t F = mix64(rk ^ R) & M;
+    const uint64_t nL = R, nR = L ^ F;
+    L = nL;
+    R = nR;
+  }
+  return (L << 20) | R;
+}
+
+__global__ void join_build_kernel(int64_t n_b, uint64_t seed, int64_t* keys, int64_t* pay) {
+  const uint64_t pk = stream_key(seed, TAG_PERM), payk = stream_key(seed, TAG_PAYLOAD);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_b;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    keys[j] = (int64_t)perm40((uint64_t)j, pk);
+    if (pay) pay[j] = uniform_in(mix64(payk + (uint64_t)j), 0, INT64_MAX);
+  }
+}
+
+__global__ void join_probe_kernel(int64_t n_p, int64_t n_b, uint64_t thr, uint64_t seed,
+                                  int64_t* keys) {
+  const uint64_t pk = stream_key(seed, TAG_PERM), hk = stream_key(seed, TAG_HIT),
+                 ck = stream_key(seed, TAG_PICK), mk = stream_key(seed, TAG_MISS);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_p;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool hit = mix64(hk + (uint64_t)i) < thr;
+    const uint64_t src = hit ? (uint64_t)uniform_in(mix64(ck + (uint64_t)i), 0, n_b - 1)
+                             : (uint64_t)uniform_in(mix64(mk + (uint64_t)i), n_b,
+                                                    (int64_t)(1ull << 40) - 1);
+    keys[i] = (int64_t)perm40(src, pk);
+  }
+}
+
+unsigned grid_for(int64_t n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = (n + 255) / 256;
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+  return (unsigned)(blocks > cap ? cap : blocks);
+}
+
 }  // namespace
+
+/* Join build side as gen.c's syn_join_build (keys distinct): keys[n_b],
+ * payload[n_b] (NULL to skip), device memory.  1 <= n_b < 2^40. */
+extern "C" int syn_gpu_join_build(int64_t n_b, uint64_t seed, int64_t* keys, int64_t* payload,
+                                  void* stream) {
+  if (n_b < 0 || n_b >= (1ll << 40) || (n_b > 0 && !keys)) return (int)cudaErrorInvalidValue;
+  if (n_b == 0) return 0;
+  join_build_kernel<<<grid_for(n_b), 256, 0, (cudaStream_t)stream>>>(n_b, seed, keys, payload);
+  return (int)cudaGetLastError();
+}
+
+/* Join probe side as gen.c's syn_join_probe (without the present flags). */
+extern "C" int syn_gpu_join_probe(int64_t n_p, int64_t n_b, uint64_t hit_threshold, uint64_t seed,
+                                  int64_t* keys, void* stream) {
+  if (n_p < 0 || n_b < 1 || n_b >= (1ll << 40) || (n_p > 0 && !keys))
+    return (int)cudaErrorInvalidValue;
+  if (n_p == 0) return 0;
+  join_probe_kernel<<<grid_for(n_p), 256, 0, (cudaStream_t)stream>>>(n_p, n_b, hit_threshold, seed,
+                                                                     keys);
+  return (int)cudaGetLastError();
+}
 
 /* keys[n] (and vals[n] unless NULL), device memory.  family 0/1/2 as above,
  * s the Zipf exponent (> 0; family 1 only), domain >= 1.  Returns a
@@ -111,13 +187,7 @@ extern "C" int syn_gpu_kv(int family, double s, int64_t n, int64_t domain, uint6
       (n > 0 && !keys) || n >= (1ll << 56))
     return (int)cudaErrorInvalidValue;
   if (n == 0) return 0;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t blocks = (n + 255) / 256;
-  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
-  if (blocks > cap) blocks = cap;
-  kv_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(family, s, n, domain, seed,
-                                                                 keys, vals);
+  kv_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(family, s, n, domain, seed, keys,
+                                                           vals);
   return (int)cudaGetLastError();
 }

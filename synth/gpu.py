@@ -52,6 +52,12 @@ def _L():
             lib.syn_gpu_kv.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
+            lib.syn_gpu_join_build.restype = ctypes.c_int
+            lib.syn_gpu_join_build.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]
+            lib.syn_gpu_join_probe.restype = ctypes.c_int
+            lib.syn_gpu_join_probe.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                               ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -86,3 +92,60 @@ def instance(seed: int, rows_lo: int = 1_000_000, rows_hi: int = 50_000_000,
 
 def instance_kv(inst: dict, device="cuda", stream=None):
     return kv(inst["fam"], inst["s"], inst["rows"], inst["domain"], inst["seed"], device, stream)
+
+
+def join_sides(n_build: int, n_probe: int, seed: int, device="cuda", stream=None,
+               hit_threshold: int | None = None):
+    """(build keys, build payload, probe keys) CUDA int64 tensors, the host
+    generator's join streams (90 % of probe rows hit by default)."""
+    import torch
+
+    from . import HIT_90
+
+    thr = HIT_90 if hit_threshold is None else hit_threshold
+    bk = torch.empty(max(n_build, 1), dtype=torch.int64, device=device)[:n_build]
+    bp = torch.empty(max(n_build, 1), dtype=torch.int64, device=device)[:n_build]
+    pk = torch.empty(max(n_probe, 1), dtype=torch.int64, device=device)[:n_probe]
+    st = (stream if stream is not None else torch.cuda.current_stream(bk.device)).cuda_stream
+    L = _L()
+    rc = L.syn_gpu_join_build(n_build, seed & (2**64 - 1), bk.data_ptr(), bp.data_ptr(), st)
+    if rc == 0:
+        rc = L.syn_gpu_join_probe(n_probe, max(1, n_build), thr, seed & (2**64 - 1),
+                                  pk.data_ptr(), st)
+    if rc != 0:
+        raise RuntimeError(f"join generator failed (cudaError {rc})")
+    return bk, bp, pk
+
+
+def batch_recipe(seed: int, n_groupby: int = 4096, n_join: int = 512) -> dict:
+    """The batched workload: group-by instances with rows log-uniform in
+    [1e3, 4e6], groups log-uniform in [1, 1e5], int32 keys at even and int64
+    keys at odd positions; join partitions with build sides log-uniform in
+    [1e3, 2.56e5] (unique keys) and probe sides log-uniform in [8e3, 2e6]
+    (90 % hits)."""
+    def lu(j, lo, hi):
+        return int(round(math.exp(math.log(lo) + _unit(seed, j) * (math.log(hi) - math.log(lo)))))
+
+    gb = []
+    for i in range(n_groupby):
+        gb.append({"rows": lu(1000 + 2 * i, 1e3, 4e6), "groups": lu(1001 + 2 * i, 1, 1e5),
+                   "key_type": "int32" if i % 2 == 0 else "int64", "seed": (seed << 20) + i})
+    jn = []
+    for i in range(n_join):
+        jn.append({"build": lu(500_000 + 2 * i, 1e3, 2.56e5),
+                   "probe": lu(500_001 + 2 * i, 8e3, 2e6), "seed": (seed << 20) + 100_000 + i})
+    return {"groupby": gb, "join": jn}
+
+
+def batch_inputs(recipe: dict, device="cuda"):
+    """Device columns of a batch recipe: ([(keys, vals)], [(bk, bp, pk)])."""
+    import torch
+
+    gb = []
+    for r in recipe["groupby"]:
+        k, v = kv(0, 0.0, r["rows"], r["groups"], r["seed"], device)
+        if r["key_type"] == "int32":
+            k = k.to(torch.int32)  # keys truncated to 32 bits
+        gb.append((k, v))
+    jn = [join_sides(r["build"], r["probe"], r["seed"], device) for r in recipe["join"]]
+    return gb, jn

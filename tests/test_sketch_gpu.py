@@ -89,3 +89,19 @@ def test_bad_hot_keys_rejected():
     with pytest.raises(rel.RelError) as e:
         rel.groupby(qc, plan=plan)
     assert e.value.status == rel.REL_E_INVALID
+
+
+def test_sketch_batched_matches_oracle():
+    names = list(CASES)
+    qs = [query_to_cuda(CASES[n]) for n in names]
+    infos = rel.sketch_batched(qs)
+    for n, s in zip(names, infos):
+        e = oracle.sketch(CASES[n])
+        for f in ("sample_rows", "kept", "ndv", "singletons", "runs", "key_min", "key_max",
+                  "key_bits"):
+            assert getattr(s, f) == e[f], (n, f)
+        assert list(s.top_key) == e["top_key"].tolist()
+        assert list(s.top_count) == e["top_count"].tolist()
+        assert bytes(s.hll) == e["hll"].tobytes()
+        single = rel.sketch(query_to_cuda(CASES[n]))
+        assert bytes(single.features) == bytes(s.features)

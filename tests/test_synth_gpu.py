@@ -64,3 +64,12 @@ def test_determinism_and_empty():
     e, f = G.kv(2, 0.0, 0, 10, seed=3)
     assert e.numel() == 0 and f.numel() == 0
 
+
+
+def test_join_sides_equal_host_streams():
+    bk, bp, pk = G.join_sides(30_001, 200_003, seed=11)
+    hk, hp = synth.join_build(30_001, seed=11)
+    hq, _ = synth.join_probe(200_003, 30_001, seed=11)
+    np.testing.assert_array_equal(bk.cpu().numpy(), hk)
+    np.testing.assert_array_equal(bp.cpu().numpy(), hp)
+    np.testing.assert_array_equal(pk.cpu().numpy(), hq)
