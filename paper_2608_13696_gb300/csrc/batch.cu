@@ -104,6 +104,7 @@ __device__ __forceinline__ void global_update(const BatchGb& g, BatchStatus* st,
       return;
     }
     s = (s + 1) & mask;
+    if ((i & 31) == 31 && ld_relaxed_u32(&st->overflow)) return;  // already overflowed
   }
   atomicOr(&st->overflow, 1u);
 }
@@ -131,6 +132,10 @@ __device__ __noinline__ void global_update_coop(const BatchGb& g, BatchStatus* s
     const uint64_t base = slot_of(k, g.log2_slots);
     bool done = false;
     for (uint32_t i = 0; i < g.max_probe && !done; i += W) {
+      if ((i & 31) == 32 - W && tile.any(ld_relaxed_u32(&st->overflow) != 0)) {
+        done = true;  // already overflowed: the result is discarded
+        break;
+      }
       const uint64_t s = (base + i + rank) & mask;
       const uint64_t cur = ld_relaxed(g.tkeys + s);
       const unsigned hit = tile.ballot(cur == k);

@@ -273,6 +273,9 @@ __device__ __forceinline__ bool gtab_update_inl(const GbParams& p, uint64_t ek,
       return true;
     }
     s = (s + 1) & mask;
+    // a long probe sequence: give up at once if the table already overflowed
+    // (the result is then discarded; this bounds the cost of an undersized plan)
+    if ((i & 31) == 31 && ld_relaxed_u32(&p.hdr->overflow)) return false;
   }
   atomicOr(&p.hdr->overflow, 1u);
   return false;
@@ -301,6 +304,7 @@ __device__ __noinline__ bool gset_insert(const GbParams& p, uint64_t ek) {
       if (k == ek) return true;
     }
     s = (s + 1) & mask;
+    if ((i & 31) == 31 && ld_relaxed_u32(&p.hdr->overflow)) return false;
   }
   atomicOr(&p.hdr->overflow, 1u);
   return false;
