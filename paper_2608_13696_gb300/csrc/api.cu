@@ -968,7 +968,7 @@ const char* rel_kernel_name(int32_t id) {
   static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
                                 "join_build", "join_probe", "join_count", "sketch", "gb_main_regs",
                                 "gb_part_hist", "gb_part_scan", "gb_part_scatter",
-                                "gb_part_agg", "mlp", "batch_a", "batch_b"};
+                                "gb_part_agg", "mlp", "batch_a", "batch_b", "gb_stream"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 
@@ -1243,6 +1243,9 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
   if (plan->variant == REL_VAR_PARTITIONED && part_shape(m.shape)) {
     if ((r = run_partitioned(p, plan, m.shape, o, ws, st))) return r;
+  } else if (!(plan->flags & REL_PLAN_GENERIC) && !plan->tile_rows &&
+             gb_stream_eligible(p, m.shape, plan->n_hot)) {
+    if ((r = gb_launch_stream(p, m.shape, st))) return r;
   } else {
     const int mode = p.tiny_ns ? MODE_TINY : MODE_LAYERED;
     if ((r = run_main(p, m.shape, mode, st))) return r;

@@ -106,6 +106,10 @@ rel_status gb_launch_compact(const GbParams& p, const GbOut& o, cudaStream_t st)
 // Partitioned variant: offsets from the histogram, then per-partition tables.
 rel_status gb_launch_part_scan(const GbParams& p, cudaStream_t st);
 rel_status gb_launch_part_agg(const GbParams& p, int shape, const GbOut& o, cudaStream_t st);
+// Streaming kernel for key/value shapes (stream.cu): pinned keys and/or a
+// small shared table in front of the global table, no staging ring.
+bool gb_stream_eligible(const GbParams& p, int shape, int n_hot);
+rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st);
 // Aggregate-array width the kernel for a shape is compiled with.
 int gb_shape_width(int shape);
 // Shared-memory bytes of the per-CTA tables (before the staging ring).

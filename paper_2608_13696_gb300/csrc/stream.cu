@@ -1,0 +1,354 @@
+// Streaming group-by for key/value rows: one int32 or int64 key column, one
+// int64 value column, aggregates (sum, count[, min, max]) -- the shapes KV4 /
+// KV2 of the fused kernel, without its staging ring.
+//
+// The paper's group-by kernels are issue-bound (Sec. 5, 7): instructions per
+// DRAM sector, not bandwidth, limit them.  This kernel keeps the per-row path
+// short.  Rows come straight from HBM in 16-byte vector loads (two rows per
+// load and column, ST_U rows per thread per chunk, evict-first), so a thread
+// has 2 x ST_U / 2 loads in flight and no shared-memory staging or barrier
+// sits on the path.  Each row then goes to the first layer that takes it:
+//  * pinned hot keys (from the sample sketch): a one-probe perfect-hash test
+//    against the pinned key, then thread-private accumulators in shared
+//    memory (one column per thread: no atomics, no bank conflicts);
+//  * optionally a CTA-shared table with shared-memory atomics;
+//  * the global table: every row still unplaced issues its first slot read
+//    before any is resolved (ST_U independent L2 round trips per thread),
+//    then claims or accumulates with CAS / RED atomics, bounded probing.
+// At the end each CTA folds its thread-private words (warp shuffles, then
+// shared atomics) and its shared table into the global table, which the
+// compaction kernel turns into the output.
+#include "groupby.cuh"
+
+namespace rel {
+
+namespace {
+
+constexpr int ST_BLOCK = 128;
+constexpr int ST_U = 8;          // rows per thread per chunk (a multiple of 2)
+// pinned keys with thread-private accumulators: 32 KB of them per CTA
+template <int NA>
+constexpr int pin_max() {
+  return NA == 4 ? 8 : 16;
+}
+constexpr int ST_PIN_LIMIT = 16;
+constexpr uint32_t ST_SMEM_MULT = 0x85EBCA77u;
+
+template <int NA>
+__device__ __forceinline__ void words_of(uint64_t v, uint64_t (&w)[NA]) {
+  w[0] = v;
+  w[1] = 1;
+  if constexpr (NA == 4) {
+    w[2] = v ^ MIN_FLIP;
+    w[3] = v ^ MAX_FLIP;
+  }
+}
+
+// word a keeps an unsigned max (MIN / MAX) rather than a sum
+template <int NA>
+__device__ __forceinline__ constexpr bool umax_word(int a) {
+  return NA == 4 && a >= 2;
+}
+
+template <int NA>
+__device__ __forceinline__ void red_global(unsigned long long* t, const uint64_t (&w)[NA]) {
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    if (umax_word<NA>(a))
+      atomicMax(t + a, (unsigned long long)w[a]);
+    else
+      atomicAdd(t + a, (unsigned long long)w[a]);
+  }
+}
+
+// Claim-or-accumulate from a first slot whose content k is already loaded.
+template <int NA>
+__device__ __forceinline__ void global_resolve(const GbParams& p, uint64_t ek, uint64_t s,
+                                               uint64_t k, const uint64_t (&w)[NA]) {
+  const uint64_t mask = (1ull << p.log2_slots) - 1;
+  for (uint32_t i = 0; i < p.max_probe; ++i) {
+    if (k == 0) {
+      k = atomicCAS((unsigned long long*)(p.tkeys + s), 0ull, (unsigned long long)ek);
+      if (k == 0) k = ek;
+    }
+    if (k == ek) {
+      red_global<NA>(p.taggs + s * (uint64_t)NA, w);
+      return;
+    }
+    s = (s + 1) & mask;
+    if ((i & 31) == 31 && ld_relaxed_u32(&p.hdr->overflow)) return;  // already overflowed
+    k = __ldcg((const unsigned long long*)(p.tkeys + s));
+  }
+  atomicOr(&p.hdr->overflow, 1u);
+}
+
+template <int NA>
+__device__ __forceinline__ void global_update(const GbParams& p, uint64_t ek,
+                                              const uint64_t (&w)[NA]) {
+  const uint64_t s = slot_of(ek, p.log2_slots);
+  global_resolve<NA>(p, ek, s, __ldcg((const unsigned long long*)(p.tkeys + s)), w);
+}
+
+template <class KT>
+struct KeyPair;
+template <>
+struct KeyPair<int64_t> {
+  using V = longlong2;
+  __device__ __forceinline__ static void split(const V& v, int64_t& a, int64_t& b) {
+    a = v.x;
+    b = v.y;
+  }
+};
+template <>
+struct KeyPair<int32_t> {
+  using V = int2;
+  __device__ __forceinline__ static void split(const V& v, int64_t& a, int64_t& b) {
+    a = v.x;
+    b = v.y;
+  }
+};
+
+template <class KT, int NA, bool PIN, bool SMT>
+__global__ void __launch_bounds__(ST_BLOCK) gb_stream_k(const __grid_constant__ GbParams p) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  // [pinned keys by slot: 32 x 8 B][dense id by slot: 32 B][key by dense id:
+  //  16 x 8 B][CTA sums: 16 x 4 x 8 B][thread-private words: PM x NA x
+  //  ST_BLOCK x 8 B][shared table keys: S x 8 B][shared table words: S x NA x 8 B]
+  constexpr int PM = pin_max<NA>();
+  uint64_t* pk = (uint64_t*)sm;
+  uint8_t* dense = sm + 256;
+  uint64_t* pkd = (uint64_t*)(sm + 288);
+  unsigned long long* csum = (unsigned long long*)(sm + 416);
+  uint64_t* acc = (uint64_t*)(sm + 416 + 8 * ST_PIN_LIMIT * 4);
+  uint64_t* sk = acc + (PIN ? PM * NA * ST_BLOCK : 0);
+  unsigned long long* sa = (unsigned long long*)(sk + (SMT ? p.smem_slots : 0));
+  const int tid = threadIdx.x;
+  const uint32_t tmask = p.tiny_slots - 1;
+
+  if (PIN) {
+    if (tid < 32) {
+      const uint64_t k = tid < (int)p.tiny_slots ? p.tiny_init[tid] : 0;
+      pk[tid] = k;
+      const unsigned occ = __ballot_sync(0xffffffffu, k != 0);
+      const int d = __popc(occ & ((1u << tid) - 1u));
+      dense[tid] = (uint8_t)d;
+      if (k != 0 && d < PM) pkd[d] = k;
+    }
+    for (int i = tid; i < PM * NA * ST_BLOCK; i += ST_BLOCK) acc[i] = 0;
+    for (int i = tid; i < PM * NA; i += ST_BLOCK) csum[i] = 0;
+  }
+  if (SMT)
+    for (uint32_t i = tid; i < p.smem_slots * (1 + NA); i += ST_BLOCK) sk[i] = 0;
+  __syncthreads();
+
+  const KT* keys = (const KT*)p.col[p.key_col[0]];
+  const int64_t* vals = (const int64_t*)p.col[p.r_a];
+  const int64_t n = p.n_rows;
+  constexpr int64_t CHUNK = (int64_t)ST_BLOCK * ST_U;
+  const bool vec = ((uintptr_t)keys % (2 * sizeof(KT)) == 0) && ((uintptr_t)vals % 16 == 0);
+
+  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n; base += (int64_t)gridDim.x * CHUNK) {
+    uint64_t ek[ST_U];
+    uint64_t val[ST_U];
+    bool ok[ST_U];
+    // rows base + j * 2 * ST_BLOCK + 2 * tid + {0, 1}: 32 lanes cover a
+    // contiguous 2 x 32-row stretch of every column per load
+    if (vec && base + CHUNK <= n) {
+#pragma unroll
+      for (int j = 0; j < ST_U / 2; ++j) {
+        const int64_t r = base + (int64_t)j * 2 * ST_BLOCK + 2 * tid;
+        const typename KeyPair<KT>::V kv = __ldcs((const typename KeyPair<KT>::V*)(keys + r));
+        const longlong2 vv = __ldcs((const longlong2*)(vals + r));
+        int64_t k0, k1;
+        KeyPair<KT>::split(kv, k0, k1);
+        ek[2 * j] = (uint64_t)k0 ^ KEY_FLIP;
+        ek[2 * j + 1] = (uint64_t)k1 ^ KEY_FLIP;
+        val[2 * j] = (uint64_t)vv.x;
+        val[2 * j + 1] = (uint64_t)vv.y;
+        ok[2 * j] = ok[2 * j + 1] = true;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < ST_U; ++j) {
+        const int64_t r = base + (int64_t)(j / 2) * 2 * ST_BLOCK + 2 * tid + (j & 1);
+        ok[j] = r < n;
+        ek[j] = ok[j] ? ((uint64_t)(int64_t)keys[r] ^ KEY_FLIP) : 0;
+        val[j] = ok[j] ? (uint64_t)vals[r] : 0;
+      }
+    }
+    bool need[ST_U];
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      need[j] = false;
+      if (!ok[j]) continue;
+      uint64_t w[NA];
+      words_of<NA>(val[j], w);
+      if (PIN) {
+        const uint32_t s = small_slot_of(ek[j], tmask, p.tiny_mult);
+        if (pk[s] == ek[j] && ek[j] != 0) {
+          uint64_t* t = acc + (size_t)dense[s] * NA * ST_BLOCK + tid;
+#pragma unroll
+          for (int a = 0; a < NA; ++a) {
+            const uint64_t o = t[a * ST_BLOCK];
+            t[a * ST_BLOCK] = umax_word<NA>(a) ? (o > w[a] ? o : w[a]) : o + w[a];
+          }
+          continue;
+        }
+      }
+      if (ek[j] == 0) {  // INT64_MIN: the side accumulator
+        atomicAdd(&p.hdr->n_side, 1ull);
+        red_global<NA>(p.hdr->side_aggs, w);
+        continue;
+      }
+      if (SMT) {
+        uint32_t s = small_slot_of(ek[j], p.smem_slots - 1, ST_SMEM_MULT);
+        bool placed = false;
+        for (uint32_t i = 0; i < p.shared_probes; ++i) {
+          uint64_t cur = *(volatile uint64_t*)(sk + s);
+          if (cur == 0) {
+            cur = atomicCAS((unsigned long long*)(sk + s), 0ull, (unsigned long long)ek[j]);
+            if (cur == 0) cur = ek[j];
+          }
+          if (cur == ek[j]) {
+            unsigned long long* t = sa + (size_t)s * NA;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+              if (umax_word<NA>(a))
+                atomicMax(t + a, (unsigned long long)w[a]);
+              else
+                atomicAdd(t + a, (unsigned long long)w[a]);
+            }
+            placed = true;
+            break;
+          }
+          s = (s + 1) & (p.smem_slots - 1);
+        }
+        if (placed) continue;
+      }
+      need[j] = true;
+    }
+    // global table: first slot reads of every remaining row, then resolve
+    uint64_t gs[ST_U], gk[ST_U];
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      if (!need[j]) continue;
+      gs[j] = slot_of(ek[j], p.log2_slots);
+      gk[j] = __ldcg((const unsigned long long*)(p.tkeys + gs[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      if (!need[j]) continue;
+      uint64_t w[NA];
+      words_of<NA>(val[j], w);
+      global_resolve<NA>(p, ek[j], gs[j], gk[j], w);
+    }
+  }
+
+  // fold the thread-private words and the shared table into the global table
+  if (PIN) {
+    const int lane = tid & 31;
+    for (int d = 0; d < PM; ++d) {
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        uint64_t x = acc[((size_t)d * NA + a) * ST_BLOCK + tid];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = umax_word<NA>(a) ? (x > y ? x : y) : x + y;
+        }
+        if (lane == 0 && x) {
+          if (umax_word<NA>(a))
+            atomicMax(csum + d * NA + a, (unsigned long long)x);
+          else
+            atomicAdd(csum + d * NA + a, (unsigned long long)x);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (PIN && tid < PM && csum[tid * NA + 1] != 0) {  // word 1 counts rows
+    uint64_t w[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) w[a] = csum[tid * NA + a];
+    global_update<NA>(p, pkd[tid], w);
+  }
+  if (SMT) {
+    for (uint32_t s = tid; s < p.smem_slots; s += ST_BLOCK) {
+      const uint64_t k = sk[s];
+      if (k == 0) continue;
+      uint64_t w[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) w[a] = sa[(size_t)s * NA + a];
+      global_update<NA>(p, k, w);
+    }
+  }
+}
+
+size_t stream_smem(int na, bool pin, bool smt, uint32_t smem_slots) {
+  size_t b = 416 + 8 * ST_PIN_LIMIT * 4;
+  if (pin) b += (size_t)8 * (na == 4 ? pin_max<4>() : pin_max<2>()) * na * ST_BLOCK;
+  if (smt) b += (size_t)8 * smem_slots * (1 + na);
+  return b;
+}
+
+template <class KT, int NA, bool PIN, bool SMT>
+rel_status launch_stream(const GbParams& p, cudaStream_t st) {
+  auto kern = gb_stream_k<KT, NA, PIN, SMT>;
+  const size_t smem = stream_smem(NA, PIN, SMT, p.smem_slots);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(stream)");
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ST_BLOCK, smem);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "occupancy(stream)");
+  if (occ < 1) return relhost::set_error("group-by: stream kernel does not fit"), REL_E_UNSUPPORTED;
+  const int64_t chunks = (p.n_rows + (int64_t)ST_BLOCK * ST_U - 1) / ((int64_t)ST_BLOCK * ST_U);
+  int64_t grid = (int64_t)relhost::device_sms() * occ;
+  if (grid > chunks) grid = chunks;
+  if (grid < 1) grid = 1;
+  relhost::launch_begin(relhost::K_GB_STREAM, st);
+  kern<<<(int)grid, ST_BLOCK, smem, st>>>(p);
+  relhost::launch_end(relhost::K_GB_STREAM, st);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(stream)");
+}
+
+template <class KT, int NA>
+rel_status dispatch_layers(const GbParams& p, cudaStream_t st) {
+  const bool pin = p.tiny_frozen && p.tiny_slots;
+  const bool smt = p.smem_slots != 0;
+  if (pin && smt) return launch_stream<KT, NA, true, true>(p, st);
+  if (pin) return launch_stream<KT, NA, true, false>(p, st);
+  if (smt) return launch_stream<KT, NA, false, true>(p, st);
+  return launch_stream<KT, NA, false, false>(p, st);
+}
+
+}  // namespace
+
+bool gb_stream_eligible(const GbParams& p, int shape, int n_hot) {
+  const bool kv = shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 || shape == SHAPE_KV2_64 ||
+                  shape == SHAPE_KV2_32;
+  if (!kv) return false;
+  // thread-private slots only when pinned (a first-come thread-private
+  // table is the fused kernel's job)
+  const int na = (shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32) ? 4 : 2;
+  const bool pin = p.tiny_slots != 0;
+  const int pmax = na == 4 ? pin_max<4>() : pin_max<2>();
+  if (pin && !(p.tiny_frozen && p.tiny_slots <= 32 && n_hot <= pmax)) return false;
+  // a large shared table would leave too few resident threads for the
+  // global probes' latency: that case stays with the fused kernel
+  return stream_smem(na, pin, p.smem_slots != 0, p.smem_slots) <= 72 * 1024;
+}
+
+rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st) {
+  if (p.n_rows == 0) return REL_OK;
+  switch (shape) {
+    case SHAPE_KV4_64: return dispatch_layers<int64_t, 4>(p, st);
+    case SHAPE_KV4_32: return dispatch_layers<int32_t, 4>(p, st);
+    case SHAPE_KV2_64: return dispatch_layers<int64_t, 2>(p, st);
+    case SHAPE_KV2_32: return dispatch_layers<int32_t, 2>(p, st);
+  }
+  relhost::set_error("group-by: stream kernel needs a key/value shape");
+  return REL_E_INVALID;
+}
+
+}  // namespace rel
