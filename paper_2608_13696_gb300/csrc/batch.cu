@@ -59,10 +59,11 @@ __device__ __forceinline__ void red_global(unsigned long long* w, int op, uint64
 }
 
 __device__ __forceinline__ void red_shared(unsigned long long* w, int op, uint64_t x) {
-  if (op == REL_MIN || op == REL_MAX)
-    atomicMax(w, (unsigned long long)x);
-  else
-    atomicAdd(w, (unsigned long long)x);
+  if (op == REL_MIN || op == REL_MAX) {
+    if (x > *(volatile unsigned long long*)w) atomicMax(w, (unsigned long long)x);
+  } else {
+    sadd64(w, x);
+  }
 }
 
 // The encoded words of one row (or of a pre-aggregated slot) for aggregate a.

@@ -256,6 +256,25 @@ __device__ __forceinline__ void red_words(const GbParams& p, unsigned long long*
   }
 }
 
+// Shared-memory words: a MIN / MAX word is read first and only raised by an
+// atomic when the row improves it -- under skew most rows of a hot key do not,
+// so most of those atomics (and their serialisation on one address) vanish.
+template <class S>
+__device__ __forceinline__ void red_words_smem(const GbParams& p, unsigned long long* w,
+                                               const Vals<S::A>& x) {
+#pragma unroll
+  for (int a = 0; a < S::A; ++a) {
+    if (live_agg<S>(p, a)) {
+      if (is_umax<S>(p, a)) {
+        if ((unsigned long long)x.v[a] > *(volatile unsigned long long*)(w + a))
+          atomicMax(w + a, (unsigned long long)x.v[a]);
+      } else {
+        sadd64(w + a, x.v[a]);
+      }
+    }
+  }
+}
+
 // Insert-or-accumulate into the global table; bounded linear probing.
 template <class S>
 __device__ __forceinline__ bool gtab_update_inl(const GbParams& p, uint64_t ek,
@@ -409,7 +428,7 @@ struct BeLayered {
       return true;
     }
     if (where == 2) {
-      red_words<S>(p, sacc + (size_t)s * A, x);
+      red_words_smem<S>(p, sacc + (size_t)s * A, x);
       return true;
     }
     if (p.tiny_slots || p.smem_slots) return gtab_update<S>(p, ek, x);
@@ -606,19 +625,21 @@ struct BePartScatter {
   static constexpr int ID = relhost::K_GB_PSCATTER;
   static constexpr int SIDE = SIDE_AGG;
   BeLayered<S> hot;           // thread-private layer (frozen) only
-  unsigned long long* cursor; // [P] next record index of this CTA per partition
+  unsigned int* cursor;       // [P] next record index of this CTA per partition
+                              // (32-bit: a partitioned input has < 2^32 rows,
+                              // and a 32-bit shared atomic is native)
   unsigned long long total;   // records the histogram counted (bound check)
   __host__ __device__ static uint64_t bytes(uint32_t tiny, uint32_t) {
-    return ((BeLayered<S>::bytes(tiny, 0) + 15) & ~15ull) + 8ull * (1u << PART_MAX_BITS);
+    return ((BeLayered<S>::bytes(tiny, 0) + 15) & ~15ull) + 4ull * (1u << PART_MAX_BITS);
   }
   __device__ void bind(uint8_t* area, const GbParams& p) {
     hot.bind(area, p);
-    cursor = (unsigned long long*)(area + ((BeLayered<S>::bytes(p.tiny_slots, 0) + 15) & ~15ull));
+    cursor = (unsigned int*)(area + ((BeLayered<S>::bytes(p.tiny_slots, 0) + 15) & ~15ull));
   }
   __device__ void init(const GbParams& p) {
     hot.init(p);
     for (uint32_t i = threadIdx.x; i < (1u << p.part_bits); i += GB_BLOCK)
-      cursor[i] = p.part_start[i] + p.hist[(size_t)i * p.fixed_grid + blockIdx.x];
+      cursor[i] = (unsigned int)(p.part_start[i] + p.hist[(size_t)i * p.fixed_grid + blockIdx.x]);
     total = p.part_start[1u << p.part_bits];
   }
   __device__ __forceinline__ bool update(const GbParams& p, uint64_t ek, const Vals<A>& x) {
@@ -630,7 +651,7 @@ struct BePartScatter {
         return true;
       }
     }
-    const unsigned long long pos = atomicAdd(&cursor[part_of(ek, p.part_bits)], 1ull);
+    const unsigned long long pos = atomicAdd(&cursor[part_of(ek, p.part_bits)], 1u);
     if (pos >= total) {  // the passes disagreed: report, never write past the buffer
       atomicOr(&p.hdr->timeout, 2u);
       return false;
@@ -918,7 +939,7 @@ __device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, uns
       if (cur == 0) cur = ek;
     }
     if (cur == ek) {
-      red_words<S>(p, ta + (size_t)s * S::A, x);
+      red_words_smem<S>(p, ta + (size_t)s * S::A, x);
       return;
     }
     s = (s + 1) & (TS - 1);
@@ -1227,9 +1248,10 @@ rel_status gb_launch_part_scan(const GbParams& p, cudaStream_t st) {
   const uint32_t P = 1u << p.part_bits;
   relhost::launch_begin(relhost::K_GB_PSCAN, st);
   gb_part_scan1<<<P, 1024, 0, st>>>(p);
+  relhost::launch_end(relhost::K_GB_PSCAN, st);
+  relhost::launch_begin(relhost::K_GB_PSCAN, st);
   gb_part_scan2<<<1, 1024, 0, st>>>(p);
   relhost::launch_end(relhost::K_GB_PSCAN, st);
-  relhost::count_launch(1);  // two kernels, one profile record
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(partition scan)");
 }

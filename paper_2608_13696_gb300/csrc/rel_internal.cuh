@@ -74,6 +74,21 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// 64-bit add to a shared-memory word from two native 32-bit atomics.  A
+// 64-bit shared-memory atomicAdd is far slower than a 32-bit one on this
+// GPU -- hundreds of times under same-address contention, as on hot keys --
+// so the low half is added atomically (returning its old value), and a
+// wrap of the low half carries into the high half.  Every wrap is seen by
+// exactly the thread whose add caused it, so the final 64-bit word is the
+// exact sum mod 2^64.  Read the word only after the adds (a barrier).
+__device__ __forceinline__ void sadd64(unsigned long long* w, uint64_t x) {
+  unsigned int* h = (unsigned int*)w;  // little-endian: h[0] low, h[1] high
+  const unsigned int lo = (unsigned int)x;
+  const unsigned int old = atomicAdd(h, lo);
+  const unsigned int hi = (unsigned int)(x >> 32) + ((unsigned int)(old + lo) < old ? 1u : 0u);
+  if (hi) atomicAdd(h + 1, hi);
+}
+
 // ------------------------------------------------------------ mbarrier / TMA
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

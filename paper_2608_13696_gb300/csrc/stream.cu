@@ -213,10 +213,12 @@ __global__ void __launch_bounds__(ST_BLOCK) gb_stream_k(const __grid_constant__ 
             unsigned long long* t = sa + (size_t)s * NA;
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
-              if (umax_word<NA>(a))
-                atomicMax(t + a, (unsigned long long)w[a]);
-              else
-                atomicAdd(t + a, (unsigned long long)w[a]);
+              if (umax_word<NA>(a)) {  // raise only when the row improves it
+                if (w[a] > *(volatile unsigned long long*)(t + a))
+                  atomicMax(t + a, (unsigned long long)w[a]);
+              } else {
+                sadd64(t + a, w[a]);
+              }
             }
             placed = true;
             break;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(ST_BLOCK) gb_stream_k(const __grid_constant__ 
           if (umax_word<NA>(a))
             atomicMax(csum + d * NA + a, (unsigned long long)x);
           else
-            atomicAdd(csum + d * NA + a, (unsigned long long)x);
+            sadd64(csum + d * NA + a, x);
         }
       }
     }
@@ -336,7 +338,7 @@ bool gb_stream_eligible(const GbParams& p, int shape, int n_hot) {
   if (pin && !(p.tiny_frozen && p.tiny_slots <= 32 && n_hot <= pmax)) return false;
   // a large shared table would leave too few resident threads for the
   // global probes' latency: that case stays with the fused kernel
-  return stream_smem(na, pin, p.smem_slots != 0, p.smem_slots) <= 72 * 1024;
+  return stream_smem(na, pin, p.smem_slots != 0, p.smem_slots) <= 80 * 1024;
 }
 
 rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st) {
