@@ -114,6 +114,19 @@ class GpuStep:
         self.results[name] = rel.groupby(q, plan=plan)
         self.results[name + ".plan"] = plan
 
+    def count_records(self):
+        """Rows a partitioned plan writes as records (not pinned, not
+        INT64_MIN) -- the partition passes' algorithmic traffic."""
+        torch = self.torch
+        for name in ("zipf", "fourkeys"):
+            plan = self.results.get(name + ".plan")
+            if plan is None or plan.variant != self.rel.VAR_PARTITIONED:
+                continue
+            k = self.q[name]["cols"][0]
+            hot = torch.tensor([plan.hot_keys[i] for i in range(plan.n_hot)] +
+                               [-(1 << 63)], dtype=torch.int64, device=k.device)
+            self.results[name + ".records"] = int(k.numel() - torch.isin(k, hot).sum().item())
+
     def result_tensors(self):
         out = []
         for name in ("lineitem", "zipf", "fourkeys"):
@@ -129,7 +142,7 @@ PARTS = ("lineitem", "join", "zipf", "fourkeys")
 def algo_bytes(kernel, part, inp, res):
     cols = {"lineitem": inp["li"]["cols"], "zipf": inp["zipf"]["cols"],
             "fourkeys": inp["four"]["cols"]}
-    if kernel.startswith("gb_main_") and kernel != "gb_main_keyset":
+    if (kernel.startswith("gb_main_") and kernel != "gb_main_keyset") or kernel == "gb_stream":
         return sum(c.nbytes for c in cols[part])
     if kernel == "gb_main_keyset":
         q = {"lineitem": inp["li"], "zipf": inp["zipf"], "fourkeys": inp["four"]}[part]
@@ -143,17 +156,17 @@ def algo_bytes(kernel, part, inp, res):
     if kernel == "join_probe":
         return inp["pk"].nbytes + res["join"][0].numel() * 16
     # partitioned variant: histogram reads the keys; scatter reads key and
-    # value and writes a 16-byte record per row; aggregation reads the
-    # records and writes the groups
+    # value and writes a 16-byte record per row that is not pinned;
+    # aggregation reads the records and writes the groups
     if part in cols:
-        n = cols[part][0].shape[0]
+        recs = res.get(part + ".records", cols[part][0].shape[0])
         if kernel == "gb_part_hist":
             return cols[part][0].nbytes
         if kernel == "gb_part_scatter":
-            return sum(c.nbytes for c in cols[part]) + 16 * n
+            return sum(c.nbytes for c in cols[part]) + 16 * recs
         if kernel == "gb_part_agg":
             k, aggs = res[part]
-            return 16 * n + k.numel() * 8 * (1 + len(aggs))
+            return 16 * recs + k.numel() * 8 * (1 + len(aggs))
     return 0
 
 
@@ -393,6 +406,7 @@ def main():
     peak_gbs = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     per_launch_ms = dms / dn
+    g.count_records()
     abytes = algo_bytes(dk, dp, inp, g.results)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
     kernels = {f"{p}/{k}": {"launches": v[0], "total_ms": v[1], "share": v[1] / total_kms}

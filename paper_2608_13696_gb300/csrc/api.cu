@@ -457,6 +457,14 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
     p.tiny_slots = 0;
     p.tiny_probes = 0;
   }
+  rel_status r;
+  if (!plan->tile_rows && gb_ppass_stream_eligible(p, shape, plan->n_hot)) {
+    if ((r = gb_launch_ppass_stream(p, shape, false, st))) return r;
+    if ((r = gb_launch_part_scan(p, st))) return r;
+    if ((r = gb_launch_ppass_stream(p, shape, true, st))) return r;
+    p.smem_slots = agg_slots;
+    return gb_launch_part_agg(p, shape, o, st);
+  }
   const bool tma = tma_ok(p);
   if (!configure_stages(p, shape, MODE_PSCATTER, tma))
     return set_error("group-by: partition scatter does not fit"), REL_E_UNSUPPORTED;
@@ -465,7 +473,6 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   p.req_stages = NS;
   if (!configure_stages(p, shape, MODE_PHIST, tma) || p.tile_rows != T)
     return set_error("group-by: partition histogram does not fit"), REL_E_UNSUPPORTED;
-  rel_status r;
   if ((r = gb_launch_main(p, shape, MODE_PHIST, tma, st))) return r;
   if ((r = gb_launch_part_scan(p, st))) return r;
   set_stages(p, T, NS);
@@ -848,7 +855,12 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
       kp.shared_probes = 4;
       cudaError_t e = cudaMemsetAsync(ws, 0, plan->scratch_bytes, st);
       if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
-      r = run_main(kp, kshape, MODE_KEYSET, st);
+      const int32_t kt = kd.cols[keys[0]].type;
+      if (!(flags & REL_PLAN_GENERIC) && kd.n_keys == 1 && kd.n_preds == 0 &&
+          (kt == REL_I64 || kt == REL_I32))
+        r = gb_launch_keyset_stream(kp, kt, st);  // streaming loads, keys only
+      else
+        r = run_main(kp, kshape, MODE_KEYSET, st);
       if (r) return r;
       HostHeader h;
       if ((r = read_header(ws, &h, st))) return r;

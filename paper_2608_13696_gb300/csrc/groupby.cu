@@ -575,11 +575,6 @@ struct BeRegs {
 
 // ------------------------------------------------- partitioned variant (P)
 
-// Partition of a stored key: top bits of a multiplicative hash independent
-// of the table hashes.
-__device__ __forceinline__ uint32_t part_of(uint64_t ek, uint32_t bits) {
-  return (uint32_t)((ek * 0xD6E8FEB86659FD93ull) >> (64 - bits));
-}
 
 __device__ __forceinline__ bool is_pinned(const GbParams& p, const uint64_t* tk, uint64_t ek) {
   if (!p.tiny_frozen) return false;
@@ -984,16 +979,11 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
     for (uint32_t i = threadIdx.x; i < TS * (1 + A); i += GB_BLOCK) tk[i] = 0;
     if (threadIdx.x == 0) ovf = nch > 1;
     __syncthreads();
-    if (nch == 1) {
-      for (unsigned long long i = beg + threadIdx.x; i < end; i += GB_BLOCK) {
-        const PartRec r = p.recs[i];
-        Vals<A> x;
-        S::from_val((uint64_t)r.val, x);
-        part_insert<S>(p, tk, ta, TS, r.ek, x, &ovf);
-      }
-    } else {
-      // heavy chunk, few distinct keys per warp: combine each key's rows in
-      // the warp first (0 is every word's identity), then one table update
+    {
+      // each warp takes 32 consecutive records at a time; the rows of the
+      // warp's first key (under skew, usually the partition's heavy key) are
+      // combined in registers first (0 is every word's identity) and applied
+      // once, the other rows go to the table one by one
       const int warp = threadIdx.x >> 5;
       for (unsigned long long b0 = beg + (unsigned long long)warp * 32; b0 < end; b0 += GB_BLOCK) {
         const unsigned long long i = b0 + lane;
@@ -1008,12 +998,12 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
 #pragma unroll
           for (int a = 0; a < A; ++a) x.v[a] = 0;
         }
-        unsigned pend = __ballot_sync(0xffffffffu, valid);
-        while (pend) {
-          const int ld = __ffs(pend) - 1;
-          const uint64_t key = __shfl_sync(0xffffffffu, ek, ld);
-          const bool mine = valid && ek == key;
-          const unsigned m = __ballot_sync(0xffffffffu, mine);
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        const int ld = __ffs(vm) - 1;  // vm != 0: b0 < end
+        const uint64_t key = __shfl_sync(0xffffffffu, ek, ld);
+        const bool mine = valid && ek == key;
+        const unsigned m = __ballot_sync(0xffffffffu, mine);
+        if (__popc(m) > 1) {
           Vals<A> y;
 #pragma unroll
           for (int a = 0; a < A; ++a) {
@@ -1027,7 +1017,9 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
             y.v[a] = v;
           }
           if (lane == ld) part_insert<S>(p, tk, ta, TS, key, y, &ovf);
-          pend &= ~m;
+          if (valid && !mine) part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
+        } else if (valid) {
+          part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
         }
       }
     }

@@ -47,6 +47,12 @@ enum GbShape : int {
   SHAPE_COUNT = 8
 };
 
+// Partition of a stored key: top bits of a multiplicative hash independent
+// of the table hashes.  The histogram and scatter passes must agree on it.
+__device__ __forceinline__ uint32_t part_of(uint64_t ek, uint32_t bits) {
+  return (uint32_t)((ek * 0xD6E8FEB86659FD93ull) >> (64 - bits));
+}
+
 struct GbParams {
   int64_t n_rows;
   int32_t n_cols, n_keys, n_preds, n_aggs;
@@ -110,6 +116,12 @@ rel_status gb_launch_part_agg(const GbParams& p, int shape, const GbOut& o, cuda
 // small shared table in front of the global table, no staging ring.
 bool gb_stream_eligible(const GbParams& p, int shape, int n_hot);
 rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st);
+// Histogram (scatter = false) or scatter pass of the partitioned variant for
+// key/value shapes, streaming; grid = p.fixed_grid CTAs in both passes.
+bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot);
+rel_status gb_launch_ppass_stream(const GbParams& p, int shape, bool scatter, cudaStream_t st);
+// Exact distinct count of one int32 / int64 key column without a filter.
+rel_status gb_launch_keyset_stream(const GbParams& p, int key_type, cudaStream_t st);
 // Aggregate-array width the kernel for a shape is compiled with.
 int gb_shape_width(int shape);
 // Shared-memory bytes of the per-CTA tables (before the staging ring).

@@ -33,6 +33,7 @@ constexpr int pin_max() {
 }
 constexpr int ST_PIN_LIMIT = 16;
 constexpr uint32_t ST_SMEM_MULT = 0x85EBCA77u;
+constexpr int ST_KS_BLOCK = 256;
 
 template <int NA>
 __device__ __forceinline__ void words_of(uint64_t v, uint64_t (&w)[NA]) {
@@ -109,7 +110,7 @@ struct KeyPair<int32_t> {
 };
 
 template <class KT, int NA, bool PIN, bool SMT>
-__global__ void __launch_bounds__(ST_BLOCK) gb_stream_k(const __grid_constant__ GbParams p) {
+__global__ void __launch_bounds__(ST_BLOCK, 6) gb_stream_k(const __grid_constant__ GbParams p) {
   extern __shared__ __align__(16) uint8_t sm[];
   // [pinned keys by slot: 32 x 8 B][dense id by slot: 32 B][key by dense id:
   //  16 x 8 B][CTA sums: 16 x 4 x 8 B][thread-private words: PM x NA x
@@ -286,6 +287,306 @@ __global__ void __launch_bounds__(ST_BLOCK) gb_stream_k(const __grid_constant__ 
   }
 }
 
+// The exact distinct count (the plain form's pre-pass) for one int32 / int64
+// key column and no filter: the same streaming loads, keys only; a CTA-shared
+// set drops the keys this CTA has already sent, every first sight goes to the
+// global key set, whose claims are the count.
+template <class KT>
+__global__ void __launch_bounds__(ST_KS_BLOCK, 4) gb_keyset_stream_k(const __grid_constant__ GbParams p) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint64_t* sk = (uint64_t*)sm;
+  const int tid = threadIdx.x;
+  const uint32_t S = p.smem_slots, smask = S - 1;
+  for (uint32_t i = tid; i < S; i += ST_KS_BLOCK) sk[i] = 0;
+  __syncthreads();
+  const KT* keys = (const KT*)p.col[p.key_col[0]];
+  const int64_t n = p.n_rows;
+  constexpr int64_t CHUNK = (int64_t)ST_KS_BLOCK * ST_U;
+  const bool vec = (uintptr_t)keys % (2 * sizeof(KT)) == 0;
+  const uint64_t mask = (1ull << p.log2_slots) - 1;
+  unsigned long long claims = 0, side = 0;
+  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n; base += (int64_t)gridDim.x * CHUNK) {
+    uint64_t ek[ST_U];
+    bool ok[ST_U];
+    if (vec && base + CHUNK <= n) {
+#pragma unroll
+      for (int j = 0; j < ST_U / 2; ++j) {
+        const int64_t r = base + (int64_t)j * 2 * ST_KS_BLOCK + 2 * tid;
+        int64_t k0, k1;
+        KeyPair<KT>::split(__ldcs((const typename KeyPair<KT>::V*)(keys + r)), k0, k1);
+        ek[2 * j] = (uint64_t)k0 ^ KEY_FLIP;
+        ek[2 * j + 1] = (uint64_t)k1 ^ KEY_FLIP;
+        ok[2 * j] = ok[2 * j + 1] = true;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < ST_U; ++j) {
+        const int64_t r = base + (int64_t)(j / 2) * 2 * ST_KS_BLOCK + 2 * tid + (j & 1);
+        ok[j] = r < n;
+        ek[j] = ok[j] ? ((uint64_t)(int64_t)keys[r] ^ KEY_FLIP) : 0;
+      }
+    }
+    bool need[ST_U];
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      need[j] = false;
+      if (!ok[j]) continue;
+      if (ek[j] == 0) {
+        ++side;
+        continue;
+      }
+      uint32_t s = small_slot_of(ek[j], smask, ST_SMEM_MULT);
+      bool seen = false, first = false;
+      for (uint32_t i = 0; i < p.shared_probes; ++i) {
+        uint64_t k = *(volatile uint64_t*)(sk + s);
+        if (k == 0) {
+          k = atomicCAS((unsigned long long*)(sk + s), 0ull, (unsigned long long)ek[j]);
+          if (k == 0) {
+            first = true;
+            break;
+          }
+        }
+        if (k == ek[j]) {
+          seen = true;
+          break;
+        }
+        s = (s + 1) & smask;
+      }
+      need[j] = first || !seen;
+    }
+    uint64_t gs[ST_U], gk[ST_U];
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      if (!need[j]) continue;
+      gs[j] = slot_of(ek[j], p.log2_slots);
+      gk[j] = __ldcg((const unsigned long long*)(p.tkeys + gs[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      if (!need[j]) continue;
+      uint64_t s = gs[j], k = gk[j];
+      bool done = false;
+      for (uint32_t i = 0; i < p.max_probe; ++i) {
+        if (k == ek[j]) {
+          done = true;
+          break;
+        }
+        if (k == 0) {
+          k = atomicCAS((unsigned long long*)(p.tkeys + s), 0ull, (unsigned long long)ek[j]);
+          if (k == 0) {
+            ++claims;
+            done = true;
+            break;
+          }
+          if (k == ek[j]) {
+            done = true;
+            break;
+          }
+        }
+        s = (s + 1) & mask;
+        if ((i & 31) == 31 && ld_relaxed_u32(&p.hdr->overflow)) {
+          done = true;  // already overflowed: the count is discarded
+          break;
+        }
+        k = __ldcg((const unsigned long long*)(p.tkeys + s));
+      }
+      if (!done) atomicOr(&p.hdr->overflow, 1u);
+    }
+  }
+  // one atomic per warp for the counts
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    claims += __shfl_xor_sync(0xffffffffu, claims, o);
+    side += __shfl_xor_sync(0xffffffffu, side, o);
+  }
+  if ((tid & 31) == 0) {
+    if (claims) atomicAdd(&p.hdr->aux, claims);
+    if (side) atomicAdd(&p.hdr->n_side, side);
+  }
+}
+
+// Partitioned variant, passes 1 and 2, streaming: a CTA counts its rows per
+// partition (pass 1), then -- after the scan turned the counts into
+// positions -- writes each row as a (key, value) record at its partition's
+// next position for this CTA (pass 2).  Pinned hot keys never become
+// records: pass 2 aggregates them in thread-private words and folds them
+// into the spill table.  INT64_MIN rows go to the side accumulator in pass 2.
+// Both passes cover the rows in the same order with the same grid, so every
+// CTA's positions are exactly the ones it counted.
+constexpr int SP_BLOCK = 256;
+
+template <class KT, int NA, bool PIN, bool SCATTER>
+__global__ void __launch_bounds__(SP_BLOCK) gb_ppass_stream_k(const __grid_constant__ GbParams p) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  constexpr int PM = pin_max<NA>();
+  uint64_t* pk = (uint64_t*)sm;
+  uint8_t* dense = sm + 256;
+  uint64_t* pkd = (uint64_t*)(sm + 288);
+  unsigned long long* csum = (unsigned long long*)(sm + 416);
+  uint64_t* acc = (uint64_t*)(sm + 416 + 8 * ST_PIN_LIMIT * 4);
+  unsigned int* ctr = (unsigned int*)(acc + ((PIN && SCATTER) ? PM * NA * SP_BLOCK : 0));
+  const int tid = threadIdx.x;
+  const uint32_t P = 1u << p.part_bits;
+  const uint32_t tmask = p.tiny_slots - 1;
+  if (PIN) {
+    if (tid < 32) {
+      const uint64_t k = tid < (int)p.tiny_slots ? p.tiny_init[tid] : 0;
+      pk[tid] = k;
+      const unsigned occ = __ballot_sync(0xffffffffu, k != 0);
+      const int d = __popc(occ & ((1u << tid) - 1u));
+      dense[tid] = (uint8_t)d;
+      if (k != 0 && d < PM) pkd[d] = k;
+    }
+    if (SCATTER) {
+      for (int i = tid; i < PM * NA * SP_BLOCK; i += SP_BLOCK) acc[i] = 0;
+      for (int i = tid; i < PM * NA; i += SP_BLOCK) csum[i] = 0;
+    }
+  }
+  for (uint32_t i = tid; i < P; i += SP_BLOCK)
+    ctr[i] = SCATTER ? (unsigned int)(p.part_start[i] + p.hist[(size_t)i * p.fixed_grid + blockIdx.x])
+                     : 0u;
+  const unsigned long long total = SCATTER ? p.part_start[P] : 0;
+  __syncthreads();
+
+  const KT* keys = (const KT*)p.col[p.key_col[0]];
+  const int64_t* vals = (const int64_t*)p.col[p.r_a];
+  const int64_t n = p.n_rows;
+  constexpr int64_t CHUNK = (int64_t)SP_BLOCK * ST_U;
+  const bool vec = ((uintptr_t)keys % (2 * sizeof(KT)) == 0) && ((uintptr_t)vals % 16 == 0);
+  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n; base += (int64_t)gridDim.x * CHUNK) {
+    uint64_t ek[ST_U];
+    uint64_t val[ST_U];
+    bool ok[ST_U];
+    if (vec && base + CHUNK <= n) {
+#pragma unroll
+      for (int j = 0; j < ST_U / 2; ++j) {
+        const int64_t r = base + (int64_t)j * 2 * SP_BLOCK + 2 * tid;
+        int64_t k0, k1;
+        KeyPair<KT>::split(__ldcs((const typename KeyPair<KT>::V*)(keys + r)), k0, k1);
+        ek[2 * j] = (uint64_t)k0 ^ KEY_FLIP;
+        ek[2 * j + 1] = (uint64_t)k1 ^ KEY_FLIP;
+        if (SCATTER) {
+          const longlong2 vv = __ldcs((const longlong2*)(vals + r));
+          val[2 * j] = (uint64_t)vv.x;
+          val[2 * j + 1] = (uint64_t)vv.y;
+        }
+        ok[2 * j] = ok[2 * j + 1] = true;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < ST_U; ++j) {
+        const int64_t r = base + (int64_t)(j / 2) * 2 * SP_BLOCK + 2 * tid + (j & 1);
+        ok[j] = r < n;
+        ek[j] = ok[j] ? ((uint64_t)(int64_t)keys[r] ^ KEY_FLIP) : 0;
+        if (SCATTER) val[j] = ok[j] ? (uint64_t)vals[r] : 0;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      if (!ok[j]) continue;
+      if (PIN) {
+        const uint32_t s = small_slot_of(ek[j], tmask, p.tiny_mult);
+        if (pk[s] == ek[j] && ek[j] != 0) {
+          if (SCATTER) {
+            uint64_t w[NA];
+            words_of<NA>(val[j], w);
+            uint64_t* t = acc + (size_t)dense[s] * NA * SP_BLOCK + tid;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+              const uint64_t o = t[a * SP_BLOCK];
+              t[a * SP_BLOCK] = umax_word<NA>(a) ? (o > w[a] ? o : w[a]) : o + w[a];
+            }
+          }
+          continue;
+        }
+      }
+      if (ek[j] == 0) {
+        if (SCATTER) {
+          uint64_t w[NA];
+          words_of<NA>(val[j], w);
+          atomicAdd(&p.hdr->n_side, 1ull);
+          red_global<NA>(p.hdr->side_aggs, w);
+        }
+        continue;
+      }
+      const uint32_t part = part_of(ek[j], p.part_bits);
+      if (!SCATTER) {
+        atomicAdd(&ctr[part], 1u);
+      } else {
+        const unsigned long long pos = atomicAdd(&ctr[part], 1u);
+        if (pos >= total) {  // the passes disagreed: report, never write past the buffer
+          atomicOr(&p.hdr->timeout, 2u);
+          continue;
+        }
+        PartRec r;
+        r.ek = ek[j];
+        r.val = (long long)val[j];
+        p.recs[pos] = r;
+      }
+    }
+  }
+  __syncthreads();
+  if (!SCATTER) {
+    for (uint32_t i = tid; i < P; i += SP_BLOCK) p.hist[(size_t)i * p.fixed_grid + blockIdx.x] = ctr[i];
+    return;
+  }
+  if (PIN) {
+    const int lane = tid & 31;
+    for (int d = 0; d < PM; ++d) {
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        uint64_t x = acc[((size_t)d * NA + a) * SP_BLOCK + tid];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
+          x = umax_word<NA>(a) ? (x > y ? x : y) : x + y;
+        }
+        if (lane == 0 && x) {
+          if (umax_word<NA>(a))
+            atomicMax(csum + d * NA + a, (unsigned long long)x);
+          else
+            sadd64(csum + d * NA + a, x);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < PM && csum[tid * NA + 1] != 0) {
+      uint64_t w[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) w[a] = csum[tid * NA + a];
+      global_update<NA>(p, pkd[tid], w);
+    }
+  }
+}
+
+size_t ppass_smem(int na, bool pin, bool scatter, uint32_t part_bits) {
+  size_t b = 416 + 8 * ST_PIN_LIMIT * 4;
+  if (pin && scatter) b += (size_t)8 * (na == 4 ? pin_max<4>() : pin_max<2>()) * na * SP_BLOCK;
+  return b + 4ull * (1u << part_bits);
+}
+
+template <class KT, int NA, bool PIN, bool SCATTER>
+rel_status launch_ppass(const GbParams& p, cudaStream_t st) {
+  auto kern = gb_ppass_stream_k<KT, NA, PIN, SCATTER>;
+  const size_t smem = ppass_smem(NA, PIN, SCATTER, p.part_bits);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(partition pass)");
+  const int id = SCATTER ? relhost::K_GB_PSCATTER : relhost::K_GB_PHIST;
+  relhost::launch_begin(id, st);
+  kern<<<p.fixed_grid, SP_BLOCK, smem, st>>>(p);
+  relhost::launch_end(id, st);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(partition pass)");
+}
+
+template <class KT, int NA>
+rel_status ppass_dispatch(const GbParams& p, bool scatter, cudaStream_t st) {
+  const bool pin = p.tiny_frozen && p.tiny_slots;
+  if (pin)
+    return scatter ? launch_ppass<KT, NA, true, true>(p, st) : launch_ppass<KT, NA, true, false>(p, st);
+  return scatter ? launch_ppass<KT, NA, false, true>(p, st) : launch_ppass<KT, NA, false, false>(p, st);
+}
+
 size_t stream_smem(int na, bool pin, bool smt, uint32_t smem_slots) {
   size_t b = 416 + 8 * ST_PIN_LIMIT * 4;
   if (pin) b += (size_t)8 * (na == 4 ? pin_max<4>() : pin_max<2>()) * na * ST_BLOCK;
@@ -339,6 +640,58 @@ bool gb_stream_eligible(const GbParams& p, int shape, int n_hot) {
   // a large shared table would leave too few resident threads for the
   // global probes' latency: that case stays with the fused kernel
   return stream_smem(na, pin, p.smem_slots != 0, p.smem_slots) <= 80 * 1024;
+}
+
+template <class KT>
+rel_status launch_keyset(const GbParams& p, cudaStream_t st) {
+  auto kern = gb_keyset_stream_k<KT>;
+  const size_t smem = 8ull * p.smem_slots;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(keyset)");
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ST_KS_BLOCK, smem);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "occupancy(keyset)");
+  if (occ < 1) return relhost::set_error("group-by: key-set kernel does not fit"), REL_E_UNSUPPORTED;
+  const int64_t chunks = (p.n_rows + (int64_t)ST_KS_BLOCK * ST_U - 1) / ((int64_t)ST_KS_BLOCK * ST_U);
+  int64_t grid = (int64_t)relhost::device_sms() * occ;
+  if (grid > chunks) grid = chunks;
+  if (grid < 1) grid = 1;
+  relhost::launch_begin(relhost::K_GB_KEYSET, st);
+  kern<<<(int)grid, ST_KS_BLOCK, smem, st>>>(p);
+  relhost::launch_end(relhost::K_GB_KEYSET, st);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(keyset)");
+}
+
+rel_status gb_launch_keyset_stream(const GbParams& p, int key_type, cudaStream_t st) {
+  if (p.n_rows == 0) return REL_OK;
+  if (p.smem_slots < 16 || (p.smem_slots & (p.smem_slots - 1)) || p.smem_slots > SHARED_MAX_SLOTS)
+    return relhost::set_error("group-by: key-set table must be a power of two in [16, 4096]"),
+           REL_E_INVALID;
+  if (key_type == REL_I64) return launch_keyset<int64_t>(p, st);
+  if (key_type == REL_I32) return launch_keyset<int32_t>(p, st);
+  return relhost::set_error("group-by: key-set kernel needs an int32 or int64 key"), REL_E_INVALID;
+}
+
+bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot) {
+  const bool kv = shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 || shape == SHAPE_KV2_64 ||
+                  shape == SHAPE_KV2_32;
+  if (!kv || p.fixed_grid < 1) return false;
+  const int na = (shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32) ? 4 : 2;
+  const int pmax = na == 4 ? pin_max<4>() : pin_max<2>();
+  if (p.tiny_slots && !(p.tiny_frozen && p.tiny_slots <= 32 && n_hot <= pmax)) return false;
+  return ppass_smem(na, p.tiny_slots != 0, true, p.part_bits) <= 200 * 1024;
+}
+
+rel_status gb_launch_ppass_stream(const GbParams& p, int shape, bool scatter, cudaStream_t st) {
+  switch (shape) {
+    case SHAPE_KV4_64: return ppass_dispatch<int64_t, 4>(p, scatter, st);
+    case SHAPE_KV4_32: return ppass_dispatch<int32_t, 4>(p, scatter, st);
+    case SHAPE_KV2_64: return ppass_dispatch<int64_t, 2>(p, scatter, st);
+    case SHAPE_KV2_32: return ppass_dispatch<int32_t, 2>(p, scatter, st);
+  }
+  relhost::set_error("group-by: partition pass needs a key/value shape");
+  return REL_E_INVALID;
 }
 
 rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st) {

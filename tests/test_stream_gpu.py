@@ -100,3 +100,61 @@ def test_overflow_reported():
     with pytest.raises(rel.RelError) as e:
         rel.groupby(qc, plan=plan)
     assert e.value.status == rel.REL_E_OVERFLOW
+
+
+@pytest.mark.parametrize("name", list(IN))
+@pytest.mark.parametrize("offset", [0, 1])
+def test_exact_count_streaming(name, offset):
+    # the exact pre-pass of a one-key, unfiltered input runs the streaming
+    # key-set kernel; its count is the number of distinct keys (INT64_MIN
+    # counted once)
+    k, v = IN[name]
+    kc = cuda(k)[offset:]
+    qc = {"cols": [kc, cuda(v)[offset:]], "keys": [0], "preds": [],
+          "aggs": [("sum", 1, [])]}
+    rel.profile_start()
+    plan = rel.plan_groupby(qc, flags=rel.PLAN_EXACT)
+    names = [n for n, _ in rel.profile_stop()]
+    assert names == ["gb_main_keyset"]
+    assert plan.est_groups == len(np.unique(k[offset:]))
+    for n in (0, 1, 1023, 1025):
+        qs = {"cols": [kc[:n], cuda(v)[offset:offset + n]], "keys": [0], "preds": [],
+              "aggs": [("sum", 1, [])]}
+        assert rel.plan_groupby(qs, flags=rel.PLAN_EXACT).est_groups == len(np.unique(k[offset:offset + n]))
+
+
+@pytest.mark.parametrize("variant", [rel.VAR_GLOBAL, rel.VAR_SMEM, rel.VAR_PARTITIONED])
+@pytest.mark.parametrize("name", ["zipf64", "uni32"])
+def test_staged_path_still_exact(name, variant):
+    # a plan that fixes the staging tile keeps the TMA-staged kernels (the
+    # streaming ones take no tile size): both paths must agree with the oracle
+    k, v = IN[name]
+    qc = {"cols": [cuda(k), cuda(v)], "keys": [0], "preds": [],
+          "aggs": [(o, 1, []) for o in OPS[4]]}
+    plan = rel.plan_groupby(qc, flags=rel.PLAN_EXACT | rel.PLAN_SKETCH | rel.plan_force(variant))
+    plan.tile_rows, plan.n_stages = 1024, 3
+    rel.profile_start()
+    keys, aggs = rel.groupby(qc, plan=plan)
+    names = [n for n, _ in rel.profile_stop()]
+    assert "gb_stream" not in names
+    ek, ea = oracle.groupby(oracle.kv_query(k, v))
+    gk, ga = canon_groupby(keys, aggs)
+    assert np.array_equal(gk, ek) and np.array_equal(ga, ea)
+
+
+@pytest.mark.parametrize("name", list(IN))
+@pytest.mark.parametrize("na", [4, 2])
+def test_partitioned_streaming_passes(name, na):
+    k, v = IN[name]
+    q = oracle.kv_query(k, v, ops=OPS[na])
+    qc = {"cols": [cuda(k), cuda(v)], "keys": [0], "preds": [],
+          "aggs": [(o, 1, []) for o in OPS[na]]}
+    for flags in (rel.PLAN_EXACT, rel.PLAN_EXACT | rel.PLAN_SKETCH):
+        plan = rel.plan_groupby(qc, flags=flags | rel.plan_force(rel.VAR_PARTITIONED))
+        rel.profile_start()
+        keys, aggs = rel.groupby(qc, plan=plan)
+        names = [n for n, _ in rel.profile_stop()]
+        assert names[:2] == ["gb_part_hist", "gb_part_scan"]
+        ek, ea = oracle.groupby(q)
+        gk, ga = canon_groupby(keys, aggs)
+        assert np.array_equal(gk, ek) and np.array_equal(ga, ea)
