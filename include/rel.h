@@ -171,7 +171,7 @@ typedef struct {
  *    otherwise: size for n_rows groups (always sufficient, rarely economical).
  *    flags & REL_PLAN_LEARNED (without a hint or REL_PLAN_EXACT): run
  *      rel_sketch, then the registered planner network (rel_planner_set) on
- *      its features; est_groups = max(ceil(1.25 * 2^y0), sample distinct
+ *      its features; est_groups = max(ceil(1.25 * 2^(y0 + 1)), sample distinct
  *      keys), the variant is the network's most likely one that the
  *      descriptor supports.  Needs rel_sketch_ws_bytes() + 2048 bytes of ws
  *      and returns REL_E_INVALID when no network is registered.  An estimate

@@ -11,6 +11,7 @@ their own (the planner's fallback).
 """
 from __future__ import annotations
 
+import ctypes
 import math
 import time
 
@@ -38,11 +39,12 @@ def learned_sizes(gb_inputs, planner_params: torch.Tensor | None = None):
     one batched network forward (the registered planner's parameters)."""
     if not gb_inputs:
         return []
-    qs = [kv_query(k, v) for k, v in gb_inputs]
-    infos = rel.sketch_batched(qs)
+    infos = rel.sketch_kv_batched([k for k, _ in gb_inputs], [v for _, v in gb_inputs])
     dev = gb_inputs[0][0].device
-    x = torch.from_numpy(np.stack([np.frombuffer(bytes(s.features), dtype=np.float32)
-                                   for s in infos])).to(dev)
+    feats = np.empty((len(infos), rel.MLP_IN), dtype=np.float32)
+    for i, s in enumerate(infos):
+        ctypes.memmove(feats[i].ctypes.data, ctypes.addressof(s.features), 4 * rel.MLP_IN)
+    x = torch.from_numpy(feats).to(dev)
     p = planner_params if planner_params is not None else rel._planner_ref[0]
     bf = torch.empty(rel.MLP_PARAMS, dtype=torch.bfloat16, device=dev)
     rel.mlp_round(p, bf)
@@ -51,8 +53,8 @@ def learned_sizes(gb_inputs, planner_params: torch.Tensor | None = None):
     for (k, _), s, yi in zip(gb_inputs, infos, y):
         n = k.numel()
         est = n
-        if math.isfinite(yi[0]):
-            est = min(n, math.ceil(2.0 ** min(max(float(yi[0]), 0.0), 62.0) * 1.25))
+        if math.isfinite(yi[0]):  # the library's learned sizing rule (2x + 25 % headroom)
+            est = min(n, math.ceil(2.0 ** (min(max(float(yi[0]), 0.0), 61.0) + 1.0) * 1.25))
         est = max(est, int(s.ndv))
         variant = 1 + int(np.argmax(yi[1:3]))  # per-CTA tables or global table
         out.append((est, next_pow2(max(16, 2 * est)), variant))

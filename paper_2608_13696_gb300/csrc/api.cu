@@ -702,6 +702,7 @@ const float* g_planner_f32 = nullptr;
 // Scratch after the sketch's: the 264 features and the 4 network outputs.
 constexpr uint64_t LEARN_SCRATCH = 2048;
 constexpr uint64_t LEARN_OUT_OFF = 1280;
+constexpr double LEARN_LOG2_MARGIN = 1.0;  // sizing headroom over the network's log2 estimate
 
 // The learned sizing step: sketch, network forward, estimate and variant.
 rel_status learned_estimate(const rel_groupby_desc* d, bool p_ok, void* ws, size_t ws_bytes,
@@ -720,11 +721,13 @@ rel_status learned_estimate(const rel_groupby_desc* d, bool p_ok, void* ws, size
   e = cudaMemcpyAsync(y, dy, sizeof y, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the planner output");
-  // 25 % headroom over the predicted count; never below the distinct keys
-  // already seen in the sample, never above the rows
+  // twice the predicted count plus 25 %: an underestimate costs a wasted run
+  // and the exact pre-pass, an overestimate only a larger table; never below
+  // the distinct keys already seen in the sample, never above the rows
   int64_t n = d->n_rows;
   if (std::isfinite(y[0])) {
-    const double g = std::ceil(std::exp2(std::min(std::max((double)y[0], 0.0), 62.0)) * 1.25);
+    const double y0 = std::min(std::max((double)y[0], 0.0), 61.0) + LEARN_LOG2_MARGIN;
+    const double g = std::ceil(std::exp2(y0) * 1.25);
     n = g < (double)d->n_rows ? (int64_t)g : d->n_rows;
   }
   if (n < info->ndv) n = info->ndv;
@@ -857,10 +860,12 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
       if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
       const int32_t kt = kd.cols[keys[0]].type;
       if (!(flags & REL_PLAN_GENERIC) && kd.n_keys == 1 && kd.n_preds == 0 &&
-          (kt == REL_I64 || kt == REL_I32))
+          (kt == REL_I64 || kt == REL_I32)) {
+        kp.smem_slots = SHARED_MAX_SLOTS;  // 32 KB set per CTA: keeps more of the hot keys
         r = gb_launch_keyset_stream(kp, kt, st);  // streaming loads, keys only
-      else
+      } else {
         r = run_main(kp, kshape, MODE_KEYSET, st);
+      }
       if (r) return r;
       HostHeader h;
       if ((r = read_header(ws, &h, st))) return r;

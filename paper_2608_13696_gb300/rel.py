@@ -17,6 +17,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -121,6 +122,31 @@ class JoinProbeDesc(ctypes.Structure):
 
 
 BATCH_MAX_AGGS = 4
+REL_BATCH_MAX_AGGS_PY = BATCH_MAX_AGGS
+
+
+def _np_fmt(t):
+    if t in (ctypes.c_void_p, ctypes.c_uint64):
+        return np.uint64
+    if t is ctypes.c_int64:
+        return np.int64
+    if t is ctypes.c_int32:
+        return np.int32
+    if t is ctypes.c_uint32:
+        return np.uint32
+    if hasattr(t, "_length_"):
+        return (_np_fmt(t._type_), (t._length_,))
+    if isinstance(t, type) and issubclass(t, ctypes._Pointer):
+        return np.uint64
+    raise TypeError(t)
+
+
+def _np_dtype(ct):
+    """A numpy dtype with the exact layout of a ctypes structure."""
+    names = [n for n, _ in ct._fields_]
+    return np.dtype({"names": names, "formats": [_np_fmt(t) for _, t in ct._fields_],
+                     "offsets": [getattr(ct, n).offset for n in names],
+                     "itemsize": ctypes.sizeof(ct)})
 
 
 class BatchGroupBy(ctypes.Structure):
@@ -524,6 +550,34 @@ def sketch_batched(qs: list, stream=None) -> list:
     return list(out)
 
 
+def sketch_kv_batched(keys: list, vals: list, ops=("sum", "count"), stream=None) -> list:
+    """sketch_batched for key/value inputs (one int32/int64 key column, one
+    int64 value column), descriptors built column-wise."""
+    L = load()
+    n = len(keys)
+    if n == 0:
+        return []
+    cols = np.zeros(2 * n, dtype=_np_dtype(Col))
+    cols["data"][0::2] = [k.data_ptr() for k in keys]
+    cols["type"][0::2] = [_DT[k.dtype] for k in keys]
+    cols["data"][1::2] = [v.data_ptr() for v in vals]
+    cols["type"][1::2] = I64
+    kc = np.zeros(1, dtype=np.int32)
+    aggs = (Agg * len(ops))(*[Agg(OPS[op], 1, 0, 0) for op in ops])
+    d = np.zeros(n, dtype=_np_dtype(GroupByDesc))
+    d["n_rows"] = [k.numel() for k in keys]
+    d["n_cols"], d["n_keys"], d["n_preds"], d["n_aggs"] = 2, 1, 0, len(ops)
+    d["cols"] = cols.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(2 * ctypes.sizeof(Col))
+    d["key_cols"] = kc.ctypes.data
+    d["preds"] = 0
+    d["aggs"] = ctypes.addressof(aggs)
+    arr = (GroupByDesc * n).from_buffer(d)
+    ws = _ws(L.rel_sketch_batched_ws_bytes(n), keys[0].device)
+    out = (SketchInfo * n)()
+    _check(L.rel_sketch_batched(arr, n, ws.data_ptr(), ws.numel(), out, _stream(stream)))
+    return list(out)
+
+
 class JoinTable:
     """A built join table; owns its workspace tensor."""
 
@@ -594,44 +648,61 @@ class Batch:
                          else self.jspec[0]["build_keys"].device if self.jspec else "cuda")
         self.device = torch.device(dev)
         ng, nj = len(self.gspec), len(self.jspec)
-        self.g = (BatchGroupBy * max(1, ng))()
-        self.j = (BatchJoinC * max(1, nj))()
-        self.gout, self.jout = [], []
-        for i, q in enumerate(self.gspec):
-            k, v = q["keys"], q.get("vals")
-            if k.dtype not in (torch.int32, torch.int64) or not k.is_contiguous():
-                raise ValueError("group-by keys must be contiguous int32/int64")
-            if v is not None and (v.dtype != torch.int64 or v.numel() != k.numel()):
-                raise ValueError("group-by values must be int64 of the keys' length")
-            ops = q["ops"]
-            cap = max(1, int(q["capacity"]))
-            ok = torch.empty(cap, dtype=torch.int64, device=self.device)
-            oa = [torch.empty(cap, dtype=torch.int64, device=self.device) for _ in ops]
-            self.gout.append((ok, oa))
-            d = self.g[i]
-            d.keys, d.vals, d.n_rows = k.data_ptr(), (v.data_ptr() if v is not None else None), k.numel()
-            d.key_type = _DT[k.dtype]
-            d.n_aggs = len(ops)
-            for a, op in enumerate(ops):
-                d.ops[a] = OPS[op]
-                d.out_aggs[a] = oa[a].data_ptr()
-            d.slots, d.est_groups = int(q["slots"]), int(q.get("est_groups", 0))
-            d.out_keys, d.out_capacity = ok.data_ptr(), cap
-        for i, q in enumerate(self.jspec):
-            bk, bp, pk = q["build_keys"], q["build_payload"], q["probe_keys"]
-            for t in (bk, bp, pk):
-                if t.dtype != torch.int64 or not t.is_contiguous():
-                    raise ValueError("join columns must be contiguous int64")
-            cap = max(1, int(q["capacity"]))
-            o = (torch.empty(cap, dtype=torch.int32, device=self.device),
-                 torch.empty(cap, dtype=torch.int32, device=self.device),
-                 torch.empty(cap, dtype=torch.int64, device=self.device))
-            self.jout.append(o)
-            d = self.j[i]
-            d.build_keys, d.build_payload, d.n_build = bk.data_ptr(), bp.data_ptr(), bk.numel()
-            d.probe_keys, d.n_probe = pk.data_ptr(), pk.numel()
-            d.out_probe_idx, d.out_build_idx, d.out_payload = (x.data_ptr() for x in o)
-            d.out_capacity = cap
+        # descriptors in numpy structured arrays laid out as the C structs
+        # (filled column-wise), outputs in a few flat tensors
+        g = np.zeros(max(1, ng), dtype=_np_dtype(BatchGroupBy))
+        j = np.zeros(max(1, nj), dtype=_np_dtype(BatchJoinC))
+        gcap = np.array([max(1, int(q["capacity"])) for q in self.gspec], dtype=np.int64)
+        gna = np.array([len(q["ops"]) for q in self.gspec], dtype=np.int64)
+        self.gk_off = np.concatenate([[0], np.cumsum(gcap)]).astype(np.int64)
+        self.ga_off = np.concatenate([[0], np.cumsum(gcap * gna)]).astype(np.int64)
+        self.gkeys = torch.empty(max(1, int(self.gk_off[-1])), dtype=torch.int64, device=self.device)
+        self.gaggs = torch.empty(max(1, int(self.ga_off[-1])), dtype=torch.int64, device=self.device)
+        if ng:
+            for q in self.gspec:
+                k, v = q["keys"], q.get("vals")
+                if k.dtype not in (torch.int32, torch.int64) or not k.is_contiguous():
+                    raise ValueError("group-by keys must be contiguous int32/int64")
+                if v is not None and (v.dtype != torch.int64 or v.numel() != k.numel()):
+                    raise ValueError("group-by values must be int64 of the keys' length")
+            g["keys"][:ng] = [q["keys"].data_ptr() for q in self.gspec]
+            g["vals"][:ng] = [q["vals"].data_ptr() if q.get("vals") is not None else 0
+                              for q in self.gspec]
+            g["n_rows"][:ng] = [q["keys"].numel() for q in self.gspec]
+            g["key_type"][:ng] = [_DT[q["keys"].dtype] for q in self.gspec]
+            g["n_aggs"][:ng] = gna
+            for i, q in enumerate(self.gspec):
+                g["ops"][i, :len(q["ops"])] = [OPS[op] for op in q["ops"]]
+            g["slots"][:ng] = [int(q["slots"]) for q in self.gspec]
+            g["est_groups"][:ng] = [int(q.get("est_groups", 0)) for q in self.gspec]
+            g["out_keys"][:ng] = self.gkeys.data_ptr() + 8 * self.gk_off[:-1]
+            base = self.gaggs.data_ptr() + 8 * self.ga_off[:-1]
+            for a in range(REL_BATCH_MAX_AGGS_PY):
+                g["out_aggs"][:ng, a] = np.where(gna > a, base + 8 * a * gcap, 0)
+            g["out_capacity"][:ng] = gcap
+        jcap = np.array([max(1, int(q["capacity"])) for q in self.jspec], dtype=np.int64)
+        self.j_off = np.concatenate([[0], np.cumsum(jcap)]).astype(np.int64)
+        tot = max(1, int(self.j_off[-1]))
+        self.jpi = torch.empty(tot, dtype=torch.int32, device=self.device)
+        self.jbi = torch.empty(tot, dtype=torch.int32, device=self.device)
+        self.jpay = torch.empty(tot, dtype=torch.int64, device=self.device)
+        if nj:
+            for q in self.jspec:
+                for t in (q["build_keys"], q["build_payload"], q["probe_keys"]):
+                    if t.dtype != torch.int64 or not t.is_contiguous():
+                        raise ValueError("join columns must be contiguous int64")
+            j["build_keys"][:nj] = [q["build_keys"].data_ptr() for q in self.jspec]
+            j["build_payload"][:nj] = [q["build_payload"].data_ptr() for q in self.jspec]
+            j["n_build"][:nj] = [q["build_keys"].numel() for q in self.jspec]
+            j["probe_keys"][:nj] = [q["probe_keys"].data_ptr() for q in self.jspec]
+            j["n_probe"][:nj] = [q["probe_keys"].numel() for q in self.jspec]
+            j["out_probe_idx"][:nj] = self.jpi.data_ptr() + 4 * self.j_off[:-1]
+            j["out_build_idx"][:nj] = self.jbi.data_ptr() + 4 * self.j_off[:-1]
+            j["out_payload"][:nj] = self.jpay.data_ptr() + 8 * self.j_off[:-1]
+            j["out_capacity"][:nj] = jcap
+        self._gnp, self._jnp = g, j
+        self.g = (BatchGroupBy * len(g)).from_buffer(g)
+        self.j = (BatchJoinC * len(j)).from_buffer(j)
         need = int(L.rel_batch_ws_bytes(self.g, ng, self.j, nj))
         if need == 0 and (ng or nj):
             raise RelError(REL_E_INVALID, "invalid batch")
@@ -686,11 +757,15 @@ class Batch:
         return [int(cnt[i]) for i in range(n)], [int(fl[i]) for i in range(n)]
 
     def groupby_output(self, i: int, n: int):
-        k, a = self.gout[i]
-        n = min(n, k.numel())
-        return k[:n], [x[:n] for x in a]
+        k0, k1 = int(self.gk_off[i]), int(self.gk_off[i + 1])
+        cap = k1 - k0
+        n = min(n, cap)
+        a0 = int(self.ga_off[i])
+        na = len(self.gspec[i]["ops"])
+        return (self.gkeys[k0:k0 + n],
+                [self.gaggs[a0 + a * cap:a0 + a * cap + n] for a in range(na)])
 
     def join_output(self, i: int, n: int):
-        pi, bi, pay = self.jout[i]
-        n = min(n, pi.numel())
-        return pi[:n], bi[:n], pay[:n]
+        o0, o1 = int(self.j_off[i]), int(self.j_off[i + 1])
+        n = min(n, o1 - o0)
+        return self.jpi[o0:o0 + n], self.jbi[o0:o0 + n], self.jpay[o0:o0 + n]

@@ -82,13 +82,13 @@ def test_underestimate_falls_back_to_exact():
 
 
 def test_estimate_rule():
-    # y0 = log2(1000): est = max(ceil(1.25 * 1000), sample distinct keys)
+    # y0 = log2(1000): est = max(ceil(1.25 * 2 * 1000), sample distinct keys)
     rel.planner_set(net([np.log2(1000.0), 0.0, 0.0, 0.0]))
-    for name, want in (("four", 1250), ("zipf", None)):
+    for name, want in (("four", 2500), ("zipf", None)):
         qc = query_to_cuda(CASES[name])
         s = rel.sketch(qc)
         plan = rel.plan_groupby(qc, flags=rel.PLAN_LEARNED)
-        assert plan.est_groups == max(1250, s.ndv)
+        assert plan.est_groups == max(2500, s.ndv)
         if want:
             assert plan.est_groups == want
     # never above the rows
