@@ -170,6 +170,26 @@ def algo_bytes(kernel, part, inp, res):
     return 0
 
 
+def dram_traffic(kernel, part, sz):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/kernel_traffic.txt, bytes per row or probe of a 5e7-row case,
+    scaled by this launch's rows); None when the kernel's source changed since
+    the capture or there is none."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    k = json.load(open(path))["kernels"].get(kernel)
+    if not k:
+        return None
+    src = os.path.join(ROOT, k["source"])
+    if hashlib.sha1(open(src, "rb").read()).hexdigest() != k["source_sha1"]:
+        return None
+    units = {"lineitem": sz["li"], "join": sz["np"], "zipf": sz["big"], "fourkeys": sz["big"]}[part]
+    return k["bytes_per_unit"] * units
+
+
 # ----------------------------------------------------------------- clocks
 
 class Clocks:
@@ -409,6 +429,7 @@ def main():
     g.count_records()
     abytes = algo_bytes(dk, dp, inp, g.results)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
+    traffic = dram_traffic(dk, dp, sz)
     kernels = {f"{p}/{k}": {"launches": v[0], "total_ms": v[1], "share": v[1] / total_kms}
                for (p, k), v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
     clocks = clk.summary()
@@ -422,7 +443,7 @@ def main():
                        "plans": "exact distinct-count pre-pass (the plain form) + 4096-row sample sketch"},
             "parts": parts,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                         "frac": achieved / peak_gbs, "traffic": None,
+                         "frac": achieved / peak_gbs, "traffic": traffic,
                          "kernel": f"{dp}/{dk}", "algo_bytes_per_launch": abytes,
                          "ms_per_launch": per_launch_ms, "peak_source": peak_src},
             "gpu_launches": launches, "kernels": kernels, "clocks": clocks}
