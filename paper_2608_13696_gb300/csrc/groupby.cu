@@ -259,13 +259,17 @@ __device__ __forceinline__ void red_words(const GbParams& p, unsigned long long*
 // Shared-memory words: a MIN / MAX word is read first and only raised by an
 // atomic when the row improves it -- under skew most rows of a hot key do not,
 // so most of those atomics (and their serialisation on one address) vanish.
-template <class S>
+template <class S, bool COUNT32 = false>
 __device__ __forceinline__ void red_words_smem(const GbParams& p, unsigned long long* w,
                                                const Vals<S::A>& x) {
 #pragma unroll
   for (int a = 0; a < S::A; ++a) {
     if (live_agg<S>(p, a)) {
-      if (is_umax<S>(p, a)) {
+      if (COUNT32 && a == 1) {
+        // key/value shapes: word 1 counts rows; below 2^32 rows per table
+        // (a partitioned input has fewer) a 32-bit add on its low half is exact
+        atomicAdd((unsigned int*)(w + 1), (unsigned int)x.v[1]);
+      } else if (is_umax<S>(p, a)) {
         if ((unsigned long long)x.v[a] > *(volatile unsigned long long*)(w + a))
           atomicMax(w + a, (unsigned long long)x.v[a]);
       } else {
@@ -934,7 +938,7 @@ __device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, uns
       if (cur == 0) cur = ek;
     }
     if (cur == ek) {
-      red_words_smem<S>(p, ta + (size_t)s * S::A, x);
+      red_words_smem<S, true>(p, ta + (size_t)s * S::A, x);
       return;
     }
     s = (s + 1) & (TS - 1);
