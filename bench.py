@@ -289,6 +289,24 @@ def sample_text(fr, sz):
 
 # ------------------------------------------------------------------- main
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (every rank calls this; world 1: unchanged)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(rows_per_step: int, world: int, steps: int, ms: float) -> float:
+    """Rows of all ranks' steps per second of the slowest rank (replicas:
+    every rank runs its own full step, weak scaling)."""
+    return rows_per_step * world * steps / (ms / 1e3)
+
+
 def run_reference(args, sz):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -395,13 +413,9 @@ def main():
         barrier()
         launches = rel.launch_count() - l0
         recs = rel.profile_stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_step = ms / args.steps
-    value = rows_step * world / (ms / 1e3) * args.steps
+    value = whole_job_rate(rows_step, world, args.steps, ms)
 
     # per part and per kernel
     parts, kern = {}, {}
@@ -540,12 +554,8 @@ def run_e2e(args, g, inp, stream, world, barrier, rows_step):
         e2e_step()
     e1.record(stream)
     barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=stream.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return {"value": rows_step * world * args.steps / (ms / 1e3), "unit": "rows/s",
+    ms = max_over_ranks(e0.elapsed_time(e1), world, stream.device)
+    return {"value": whole_job_rate(rows_step, world, args.steps, ms), "unit": "rows/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h[0],
             "ms_per_step": ms / args.steps}
 

@@ -145,3 +145,93 @@ def test_join_argument_checks(L):
     # an unbuilt handle is rejected
     assert L.rel_join_probe(ctypes.byref(t), 0x10, 10, 0x10, 0x10, 0x10, 10, ctypes.byref(n),
                             None) == rel.REL_E_INVALID
+
+
+def test_planner_and_mlp_sizes_and_checks(L):
+    # backward scratch: dz1, dz2, dout per sample (132 floats)
+    assert L.rel_mlp_ws_bytes(256) == 256 * 132 * 4
+    assert L.rel_mlp_ws_bytes(0) == 132 * 4
+    assert L.rel_mlp_ws_bytes(-1) == 0
+    # AdamW rejects a step < 1 and betas outside [0, 1) before any launch
+    p = ctypes.c_void_p(0x1000)
+    assert L.rel_mlp_adamw(p, p, p, p, p, 0, 1e-3, 0.9, 0.999, 1e-8, 0.0, None) == rel.REL_E_INVALID
+    assert L.rel_mlp_adamw(p, p, p, p, p, 1, 1e-3, 1.0, 0.999, 1e-8, 0.0, None) == rel.REL_E_INVALID
+    assert L.rel_mlp_forward(None, None, None, -1, None, None, None) == rel.REL_E_INVALID
+    # the planner takes both parameter copies or neither
+    assert L.rel_planner_set(p, None) == rel.REL_E_INVALID
+    assert L.rel_planner_set(None, None) == rel.REL_OK
+
+
+def test_learned_plan_needs_a_network_and_scratch(L):
+    d, keep = _desc(100)
+    plan = rel.Plan()
+    assert L.rel_planner_set(None, None) == rel.REL_OK
+    # without workspace: the scratch size comes back (sketch + 2 KB) before any GPU work
+    r = L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), rel.PLAN_LEARNED, 0, None, 0,
+                        ctypes.byref(plan), None)
+    assert r == rel.REL_E_CAPACITY
+    assert plan.scratch_bytes == L.rel_sketch_ws_bytes() + 2048
+
+
+def test_forced_partitioned_needs_key_value_shape(L):
+    cols = (rel.Col * 3)(rel.Col(0x1000, rel.I64, 0), rel.Col(0x2000, rel.I64, 0),
+                         rel.Col(0x3000, rel.I32, 0))
+    keys = (ctypes.c_int32 * 1)(0)
+    aggs = (rel.Agg * 1)(rel.Agg(rel.OPS["sum"], 1, 0, 0))
+    preds = (rel.RangePred * 1)(rel.RangePred(2, 0, 0, 10))
+    d = rel.GroupByDesc(100, 3, 1, 1, 1, cols, keys, preds, aggs)  # a filter: not key/value
+    plan = rel.Plan()
+    r = L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d),
+                        rel.plan_force(rel.VAR_PARTITIONED), 10, None, 0, ctypes.byref(plan), None)
+    assert r == rel.REL_E_UNSUPPORTED
+
+
+def test_auto_workspace_bound(L):
+    d, keep = _desc(1_000_000)
+    need = L.rel_groupby_auto_ws_bytes(ctypes.byref(d))
+    # at least the layered table for 2n slots and the partition records
+    assert need >= 256 + (1 << 21) * 16
+    assert need >= 16 * 1_000_000
+    bad, keep2 = _desc(-1)
+    assert L.rel_groupby_auto_ws_bytes(ctypes.byref(bad)) == 0
+
+
+def _batch_arrays(n_rows=1000, slots=2048, cap=100, key_type=None):
+    g = (rel.BatchGroupBy * 1)()
+    g[0].keys, g[0].vals, g[0].n_rows = 0x1000, 0x2000, n_rows
+    g[0].key_type = rel.I64 if key_type is None else key_type
+    g[0].n_aggs = 2
+    g[0].ops[0], g[0].ops[1] = rel.OPS["sum"], rel.OPS["count"]
+    g[0].slots, g[0].est_groups = slots, 10
+    g[0].out_keys, g[0].out_capacity = 0x3000, cap
+    g[0].out_aggs[0], g[0].out_aggs[1] = 0x4000, 0x5000
+    j = (rel.BatchJoinC * 1)()
+    j[0].build_keys, j[0].build_payload, j[0].n_build = 0x6000, 0x7000, 500
+    j[0].probe_keys, j[0].n_probe = 0x8000, 4000
+    j[0].out_probe_idx, j[0].out_build_idx, j[0].out_payload = 0x9000, 0xa000, 0xb000
+    j[0].out_capacity = 4000
+    return g, j
+
+
+def test_batch_sizes_and_validation(L):
+    g, j = _batch_arrays()
+    need = L.rel_batch_ws_bytes(g, 1, j, 1)
+    # tables: 2048 slots x (8 + 2 x 8) B, 1024 join slots x 24 B, side list 500 x 16 B
+    assert need >= 2048 * 24 + 1024 * 24 + 500 * 16
+    assert L.rel_batch_ws_bytes(g, 0, j, 0) > 0
+    bad, j2 = _batch_arrays(slots=1000)          # not a power of two
+    assert L.rel_batch_ws_bytes(bad, 1, j2, 1) == 0
+    bad, j2 = _batch_arrays(key_type=rel.U8)     # u8 keys are not a key/value batch
+    assert L.rel_batch_ws_bytes(bad, 1, j2, 1) == 0
+    h = rel.BatchHandle()
+    for cfg in ((100, 8, 1, 0), (256, 3, 1, 0), (256, 8, 3, 0), (256, 8, 1, 4096)):
+        c = rel.BatchConfig(*cfg)
+        r = L.rel_batch_prepare(g, 1, j, 1, ctypes.byref(c), ctypes.c_void_p(0x10000), need,
+                                ctypes.byref(h), None)
+        assert r == rel.REL_E_INVALID, cfg
+    c = rel.BatchConfig(256, 8, 1, 0)
+    r = L.rel_batch_prepare(g, 1, j, 1, ctypes.byref(c), ctypes.c_void_p(0x10000), need - 1,
+                            ctypes.byref(h), None)
+    assert r == rel.REL_E_CAPACITY
+    # a handle that prepare never filled is refused
+    assert L.rel_batch_run(ctypes.byref(rel.BatchHandle()), None) == rel.REL_E_INVALID
