@@ -222,10 +222,20 @@ rel_status join_launch_probe(const JoinParams& p, const JoinOut& o, const int64_
                              int64_t n, bool emit, cudaStream_t st) {
   if (n == 0) return REL_OK;
   const int id = emit ? relhost::K_JOIN_PROBE : relhost::K_JOIN_COUNT;
-  relhost::launch_begin(id, st);
+  // one wave of resident CTAs, each walking the tiles: a second, partial
+  // wave would leave most SMs idle at the end
+  static int occ[2] = {0, 0};
+  int& o_ = occ[emit ? 1 : 0];
+  if (o_ == 0) {
+    const cudaError_t e0 =
+        emit ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_, join_probe_fast_k<true>, J_BLOCK, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_, join_probe_fast_k<false>, J_BLOCK, 0);
+    if (e0 != cudaSuccess || o_ < 1) o_ = 4;
+  }
   const int64_t tiles = (n + (int64_t)J_BLOCK * J_IT - 1) / ((int64_t)J_BLOCK * J_IT);
-  int64_t g = (int64_t)relhost::device_sms() * 8;
+  int64_t g = (int64_t)relhost::device_sms() * o_;
   if (g > tiles) g = tiles;
+  relhost::launch_begin(id, st);
   if (emit)
     join_probe_fast_k<true><<<(int)g, J_BLOCK, 0, st>>>(p, o, probe, n);
   else
