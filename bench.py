@@ -49,8 +49,8 @@ def full_sizes(small: bool):
 def make_inputs(sz, seed, prefix=None):
     """Seeded inputs; with prefix = {part: fraction} only those leading rows
     (identical to the full columns' prefixes: the generator is counter-based)."""
-    import oracle  # query description helpers only; no oracle computation here
     import synth
+    from paper_2608_13696_gb300.workloads import kv_query, lineitem_query
 
     f = prefix or {}
     n = lambda key, part: max(1, int(sz[key] * f.get(part, 1.0)))
@@ -59,8 +59,8 @@ def make_inputs(sz, seed, prefix=None):
     pk, _ = synth.join_probe(n("np", "join"), sz["nb"], seed=seed)
     zk, zv = synth.zipf_kv(n("big", "zipf"), seed=seed)
     fk, fv = synth.few_keys_kv(n("big", "fourkeys"), n_keys=4, seed=seed)
-    return {"li": oracle.lineitem_query(li), "bk": bk, "bp": bp, "pk": pk,
-            "zipf": oracle.kv_query(zk, zv), "four": oracle.kv_query(fk, fv)}
+    return {"li": lineitem_query(li), "bk": bk, "bp": bp, "pk": pk,
+            "zipf": kv_query(zk, zv), "four": kv_query(fk, fv)}
 
 
 def part_rows(sz):
