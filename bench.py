@@ -170,24 +170,24 @@ def algo_bytes(kernel, part, inp, res):
     return 0
 
 
-def dram_traffic(kernel, part, sz):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture
-    (profiles/kernel_traffic.txt, bytes per row or probe of a 5e7-row case,
-    scaled by this launch's rows); None when the kernel's source changed since
-    the capture or there is none."""
+def captured(kernel, part, sz):
+    """(DRAM bytes, warp instructions) per launch of `kernel` from the
+    committed ncu capture (profiles/kernel_traffic.txt: per row or probe of a
+    5e7-row case, scaled by this launch's rows); (None, None) when the
+    kernel's source changed since the capture or there is none."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "kernel_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return None, None
     k = json.load(open(path))["kernels"].get(kernel)
     if not k:
-        return None
+        return None, None
     src = os.path.join(ROOT, k["source"])
     if hashlib.sha1(open(src, "rb").read()).hexdigest() != k["source_sha1"]:
-        return None
+        return None, None
     units = {"lineitem": sz["li"], "join": sz["np"], "zipf": sz["big"], "fourkeys": sz["big"]}[part]
-    return k["bytes_per_unit"] * units
+    return k["bytes_per_unit"] * units, k.get("warp_inst_per_unit", 0.0) * units or None
 
 
 # ----------------------------------------------------------------- clocks
@@ -443,7 +443,7 @@ def main():
     g.count_records()
     abytes = algo_bytes(dk, dp, inp, g.results)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
-    traffic = dram_traffic(dk, dp, sz)
+    traffic, winst = captured(dk, dp, sz)
     kernels = {f"{p}/{k}": {"launches": v[0], "total_ms": v[1], "share": v[1] / total_kms}
                for (p, k), v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
     clocks = clk.summary()
@@ -461,6 +461,20 @@ def main():
                          "kernel": f"{dp}/{dk}", "algo_bytes_per_launch": abytes,
                          "ms_per_launch": per_launch_ms, "peak_source": peak_src},
             "gpu_launches": launches, "kernels": kernels, "clocks": clocks}
+    # the paper's instruction roofline (Sec. 2.2): warp instructions per second
+    # against N_SM x 4 schedulers x the SM clock sampled during the run, and
+    # warp instructions per 32-byte DRAM sector (the ridge is peak issue /
+    # (DRAM bandwidth / 32 B))
+    if winst and clocks.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = sms * 4 * clocks["sm_mhz"] * 1e6
+        inst_rate = winst / (per_launch_ms / 1e3)
+        line["instr_roofline"] = {
+            "kernel": f"{dp}/{dk}", "achieved_warp_inst_per_s": inst_rate,
+            "peak_warp_inst_per_s": issue_peak, "frac": inst_rate / issue_peak,
+            "warp_inst_per_sector": winst / (traffic / 32) if traffic else None,
+            "ridge_inst_per_sector": issue_peak / (peak_gbs * 1e9 / 32),
+            "n_sm": sms, "sm_mhz": clocks["sm_mhz"], "source": "profiles/kernel_traffic.txt"}
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, g, inp, stream, world, barrier, rows_step)
