@@ -1007,10 +1007,13 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
         const uint64_t key = __shfl_sync(0xffffffffu, ek, ld);
         const bool mine = valid && ek == key;
         const unsigned m = __ballot_sync(0xffffffffu, mine);
-        if (__popc(m) > 1) {
-          Vals<A> y;
+        const bool combine = __popc(m) > 1;  // uniform across the warp
+        if (combine) {
+          // the first key's words over its lanes; its count is the lanes'
+          // number (word 1 of the key/value shapes counts rows)
 #pragma unroll
           for (int a = 0; a < A; ++a) {
+            if (a == 1 && !S::RT) continue;
             const bool um = is_umax<S>(p, a);
             uint64_t v = mine ? x.v[a] : 0ull;
 #pragma unroll
@@ -1018,13 +1021,14 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
               const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
               v = um ? (v > w ? v : w) : v + w;
             }
-            y.v[a] = v;
+            if (lane == ld) x.v[a] = v;
           }
-          if (lane == ld) part_insert<S>(p, tk, ta, TS, key, y, &ovf);
-          if (valid && !mine) part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
-        } else if (valid) {
-          part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
+          if (!S::RT && lane == ld) x.v[1] = (uint64_t)__popc(m);
         }
+        // one insert per lane in one converged call: the first key's lane
+        // brings the combined words, the other keys' lanes their own row,
+        // the first key's other lanes nothing
+        if (valid && (!combine || !mine || lane == ld)) part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
       }
     }
     __syncthreads();
