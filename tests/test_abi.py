@@ -235,3 +235,13 @@ def test_batch_sizes_and_validation(L):
     assert r == rel.REL_E_CAPACITY
     # a handle that prepare never filled is refused
     assert L.rel_batch_run(ctypes.byref(rel.BatchHandle()), None) == rel.REL_E_INVALID
+
+
+@pytest.mark.parametrize("ct", [rel.Col, rel.GroupByDesc, rel.BatchGroupBy, rel.BatchJoinC])
+def test_numpy_layouts_match_ctypes(ct):
+    # the batch and batched-sketch descriptors are filled column-wise in numpy
+    # arrays that must have the C structs' exact layout
+    dt = rel._np_dtype(ct)
+    assert dt.itemsize == ctypes.sizeof(ct)
+    for name, _ in ct._fields_:
+        assert dt.fields[name][1] == getattr(ct, name).offset, name

@@ -1,0 +1,61 @@
+"""Host-side pieces of bench.py: algorithmic bytes per kernel and the use of
+the committed capture (void once a kernel's source changed)."""
+import hashlib
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _inp():
+    n = 1000
+    z = np.zeros(n, np.int64)
+    li = [np.zeros(n, np.uint8), np.zeros(n, np.uint8)] + [z] * 4 + [np.zeros(n, np.int32)]
+    return {"li": {"cols": li, "keys": [0, 1], "preds": [(6, 0, 1)]},
+            "zipf": {"cols": [z, z], "keys": [0], "preds": []},
+            "four": {"cols": [z, z], "keys": [0], "preds": []},
+            "bk": z[:10], "bp": z[:10], "pk": z}
+
+
+class _T:
+    def __init__(self, n):
+        self.n = n
+
+    def numel(self):
+        return self.n
+
+
+def test_algorithmic_bytes():
+    inp = _inp()
+    res = {"zipf": (_T(7), [_T(7)] * 4), "join": (_T(900), _T(900), _T(900)),
+           "zipf.records": 600}
+    assert bench.algo_bytes("gb_stream", "zipf", inp, res) == 16_000
+    assert bench.algo_bytes("gb_main_keyset", "zipf", inp, res) == 8_000
+    assert bench.algo_bytes("gb_main_keyset", "lineitem", inp, res) == 1000 * (1 + 1 + 4)
+    assert bench.algo_bytes("gb_part_hist", "zipf", inp, res) == 8_000
+    assert bench.algo_bytes("gb_part_scatter", "zipf", inp, res) == 16_000 + 16 * 600
+    assert bench.algo_bytes("gb_part_agg", "zipf", inp, res) == 16 * 600 + 7 * 8 * 5
+    assert bench.algo_bytes("join_probe", "join", inp, res) == 8_000 + 900 * 16
+    assert bench.algo_bytes("sketch", "zipf", inp, res) == 0
+
+
+def test_capture_scaling_and_staleness(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source")
+    (tmp_path / "profiles").mkdir()
+    doc = {"kernels": {"gb_stream": {"source": str(src),
+                                     "source_sha1": hashlib.sha1(b"kernel source").hexdigest(),
+                                     "bytes_per_unit": 16.5, "warp_inst_per_unit": 2.0}}}
+    (tmp_path / "profiles" / "kernel_traffic.txt").write_text(json.dumps(doc))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sz = bench.full_sizes(True)
+    traffic, inst = bench.captured("gb_stream", "zipf", sz)
+    assert traffic == 16.5 * sz["big"] and inst == 2.0 * sz["big"]
+    assert bench.captured("gb_part_agg", "zipf", sz) == (None, None)
+    src.write_text("kernel source, changed")
+    assert bench.captured("gb_stream", "zipf", sz) == (None, None)

@@ -81,3 +81,21 @@ def test_gpu_instance_recipe_ranges():
         fams.add(inst["family"])
         assert G.instance(seed) == inst
     assert fams == {f[0] for f in G.FAMILIES}
+
+
+def test_batch_recipe_ranges_and_determinism():
+    from synth import gpu as G
+
+    r = G.batch_recipe(0)
+    assert len(r["groupby"]) == 4096 and len(r["join"]) == 512
+    rows = [x["rows"] for x in r["groupby"]]
+    assert min(rows) >= 1000 and max(rows) <= 4_000_000
+    assert all(1 <= x["groups"] <= 100_000 for x in r["groupby"])
+    assert [x["key_type"] for x in r["groupby"][:4]] == ["int32", "int64", "int32", "int64"]
+    assert all(1000 <= x["build"] <= 256_000 and 8000 <= x["probe"] <= 2_000_000
+               for x in r["join"])
+    # log-uniform rows: about 2e9 in all (mean (4e6 - 1e3) / ln 4000)
+    assert 1.6e9 < sum(rows) < 2.4e9
+    assert G.batch_recipe(0) == r and G.batch_recipe(1) != r
+    seeds = [x["seed"] for x in r["groupby"]] + [x["seed"] for x in r["join"]]
+    assert len(set(seeds)) == len(seeds)
