@@ -174,7 +174,8 @@ def captured(kernel, part, sz):
     """(DRAM bytes, warp instructions) per launch of `kernel` from the
     committed ncu capture (profiles/kernel_traffic.txt: per row or probe of a
     5e7-row case, scaled by this launch's rows); (None, None) when the
-    kernel's source changed since the capture or there is none."""
+    kernel's source or its launch's host code changed since the capture, or
+    there is none."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "kernel_traffic.txt")
@@ -183,9 +184,13 @@ def captured(kernel, part, sz):
     k = json.load(open(path))["kernels"].get(kernel)
     if not k:
         return None, None
-    src = os.path.join(ROOT, k["source"])
-    if hashlib.sha1(open(src, "rb").read()).hexdigest() != k["source_sha1"]:
-        return None, None
+    # the kernel's source and the host code that sizes its launch (tables,
+    # grid) must be the ones the counters were taken from
+    srcs = k.get("sources") or {k["source"]: k["source_sha1"]}
+    for rel_path, digest in srcs.items():
+        src = os.path.join(ROOT, rel_path)
+        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != digest:
+            return None, None
     units = {"lineitem": sz["li"], "join": sz["np"], "zipf": sz["big"], "fourkeys": sz["big"]}[part]
     return k["bytes_per_unit"] * units, k.get("warp_inst_per_unit", 0.0) * units or None
 

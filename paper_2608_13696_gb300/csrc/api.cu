@@ -699,6 +699,9 @@ void sketch_fill(const rel_groupby_desc* d, const DevSketch& h, int bits, rel_sk
 const void* g_planner_bf16 = nullptr;
 const float* g_planner_f32 = nullptr;
 
+// slots of the exact pre-pass's first key set (8 bytes each: 128 MB, L2-sized)
+constexpr uint64_t EXACT_SET_L2_SLOTS = 1ull << 24;
+
 // Scratch after the sketch's: the 264 features and the 4 network outputs.
 constexpr uint64_t LEARN_SCRATCH = 2048;
 constexpr uint64_t LEARN_OUT_OFF = 1280;
@@ -852,26 +855,38 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
       }
       kp.hdr = (WsHeader*)ws;
       kp.tkeys = (uint64_t*)((uint8_t*)ws + HEADER_BYTES);
-      kp.log2_slots = log2_pow2(set_slots);
-      kp.max_probe = (uint32_t)(set_slots < 4096 ? set_slots : 4096);
-      kp.smem_slots = 2048;
-      kp.shared_probes = 4;
-      cudaError_t e = cudaMemsetAsync(ws, 0, plan->scratch_bytes, st);
-      if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
       const int32_t kt = kd.cols[keys[0]].type;
-      if (!(flags & REL_PLAN_GENERIC) && kd.n_keys == 1 && kd.n_preds == 0 &&
-          (kt == REL_I64 || kt == REL_I32)) {
-        kp.smem_slots = SHARED_MAX_SLOTS;  // 32 KB set per CTA: keeps more of the hot keys
-        r = gb_launch_keyset_stream(kp, kt, st);  // streaming loads, keys only
-      } else {
-        r = run_main(kp, kshape, MODE_KEYSET, st);
+      const bool stream_keys = !(flags & REL_PLAN_GENERIC) && kd.n_keys == 1 &&
+                               kd.n_preds == 0 && (kt == REL_I64 || kt == REL_I32);
+      // First a key set of at most EXACT_SET_L2_SLOTS slots (128 MB: its
+      // probes stay in L2, and the memset is small); only when the distinct
+      // keys overflow it, the full 2 x rows set.  Both give the same count.
+      uint64_t try_slots = set_slots < EXACT_SET_L2_SLOTS ? set_slots : EXACT_SET_L2_SLOTS;
+      for (;;) {
+        kp.log2_slots = log2_pow2(try_slots);
+        kp.max_probe = (uint32_t)(try_slots < 4096 ? try_slots : 4096);
+        kp.smem_slots = 2048;
+        kp.shared_probes = 4;
+        cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + 8ull * try_slots, st);
+        if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+        if (stream_keys) {
+          kp.smem_slots = SHARED_MAX_SLOTS;  // 32 KB set per CTA: keeps more of the hot keys
+          r = gb_launch_keyset_stream(kp, kt, st);  // streaming loads, keys only
+        } else {
+          r = run_main(kp, kshape, MODE_KEYSET, st);
+        }
+        if (r) return r;
+        HostHeader h;
+        if ((r = read_header(ws, &h, st))) return r;
+        if (h.timeout) return set_error("plan: a device wait timed out"), REL_E_TIMEOUT;
+        if (h.overflow && try_slots < set_slots) {
+          try_slots = set_slots;
+          continue;
+        }
+        if (h.overflow) return set_error("plan: key set overflow"), REL_E_OVERFLOW;
+        est = (int64_t)h.aux + (h.n_side > 0 ? 1 : 0);
+        break;
       }
-      if (r) return r;
-      HostHeader h;
-      if ((r = read_header(ws, &h, st))) return r;
-      if (h.timeout) return set_error("plan: a device wait timed out"), REL_E_TIMEOUT;
-      if (h.overflow) return set_error("plan: key set overflow"), REL_E_OVERFLOW;
-      est = (int64_t)h.aux + (h.n_side > 0 ? 1 : 0);
     }
   } else {
     est = d->n_rows;

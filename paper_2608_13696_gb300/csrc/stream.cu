@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(ST_BLOCK, 6) gb_stream_k(const __grid_constant
 // The exact distinct count (the plain form's pre-pass) for one int32 / int64
 // key column and no filter: the same streaming loads, keys only; a CTA-shared
 // set drops the keys this CTA has already sent, every first sight goes to the
-// global key set, whose claims are the count.
+// global key set, whose claims are the count.  Once the set has overflowed
+// the count is void (the caller retries with a larger set), so a thread that
+// sees the overflow stops reading.
 template <class KT>
 __global__ void __launch_bounds__(ST_KS_BLOCK, 4) gb_keyset_stream_k(const __grid_constant__ GbParams p) {
   extern __shared__ __align__(16) uint8_t sm[];
@@ -305,7 +307,9 @@ __global__ void __launch_bounds__(ST_KS_BLOCK, 4) gb_keyset_stream_k(const __gri
   const bool vec = (uintptr_t)keys % (2 * sizeof(KT)) == 0;
   const uint64_t mask = (1ull << p.log2_slots) - 1;
   unsigned long long claims = 0, side = 0;
-  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n; base += (int64_t)gridDim.x * CHUNK) {
+  bool stop = false;  // the set overflowed: the count is void, so stop reading
+  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n && !stop;
+       base += (int64_t)gridDim.x * CHUNK) {
     uint64_t ek[ST_U];
     bool ok[ST_U];
     if (vec && base + CHUNK <= n) {
@@ -385,12 +389,15 @@ __global__ void __launch_bounds__(ST_KS_BLOCK, 4) gb_keyset_stream_k(const __gri
         }
         s = (s + 1) & mask;
         if ((i & 31) == 31 && ld_relaxed_u32(&p.hdr->overflow)) {
-          done = true;  // already overflowed: the count is discarded
+          done = stop = true;  // already overflowed: the count is discarded
           break;
         }
         k = __ldcg((const unsigned long long*)(p.tkeys + s));
       }
-      if (!done) atomicOr(&p.hdr->overflow, 1u);
+      if (!done) {
+        atomicOr(&p.hdr->overflow, 1u);
+        stop = true;
+      }
     }
   }
   // one atomic per warp for the counts

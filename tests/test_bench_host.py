@@ -59,3 +59,22 @@ def test_capture_scaling_and_staleness(tmp_path, monkeypatch):
     assert bench.captured("gb_part_agg", "zipf", sz) == (None, None)
     src.write_text("kernel source, changed")
     assert bench.captured("gb_stream", "zipf", sz) == (None, None)
+
+
+def test_capture_void_when_launch_host_code_changes(tmp_path, monkeypatch):
+    kern, host = tmp_path / "k.cu", tmp_path / "api.cu"
+    kern.write_text("kernel source")
+    host.write_text("table sizing")
+    (tmp_path / "profiles").mkdir()
+    sha = lambda b: hashlib.sha1(b).hexdigest()
+    doc = {"kernels": {"gb_main_keyset": {
+        "sources": {str(kern): sha(b"kernel source"), str(host): sha(b"table sizing")},
+        "bytes_per_unit": 10.0, "warp_inst_per_unit": 4.0}}}
+    (tmp_path / "profiles" / "kernel_traffic.txt").write_text(json.dumps(doc))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sz = bench.full_sizes(True)
+    assert bench.captured("gb_main_keyset", "zipf", sz) == (10.0 * sz["big"], 4.0 * sz["big"])
+    host.write_text("table sizing, changed")
+    assert bench.captured("gb_main_keyset", "zipf", sz) == (None, None)
+    host.unlink()
+    assert bench.captured("gb_main_keyset", "zipf", sz) == (None, None)

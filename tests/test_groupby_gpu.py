@@ -212,3 +212,31 @@ def test_full_size_four_keys_200m():
     sample = np.array([synth.mix64_signed(r) for r in (1, 2)])
     plan = _big_checks(keys, vals, rel.PLAN_EXACT, sample)
     assert plan.est_groups == 4 and plan.tiny_slots == 8
+
+
+@pytest.mark.parametrize("key_type,generic", [("int64", False), ("int32", False), ("int64", True)])
+def test_exact_count_beyond_the_l2_sized_set(key_type, generic):
+    """2.4e7 rows of ~2.4e7 distinct keys: more than the exact pre-pass's
+    first, L2-sized key set holds (2^24 slots), so it overflows and the count
+    comes from the full-size set -- still the exact number of distinct keys."""
+    from synth import gpu as G
+
+    n = 24_000_000
+    k, v = G.kv(0, 0.0, n, 10**15, seed=11)
+    if key_type == "int32":
+        k = k.to(torch.int32)
+    q = {"cols": [k, v], "keys": [0], "preds": [], "aggs": [("count", 1, [])]}
+    plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT | (rel.PLAN_GENERIC if generic else 0))
+    distinct = np.unique(k.cpu().numpy()).size
+    assert distinct > (1 << 24)
+    assert plan.est_groups == distinct
+
+
+def test_exact_count_within_the_l2_sized_set():
+    """2.4e7 rows over 1e7 keys: the first key set holds them all."""
+    from synth import gpu as G
+
+    k, v = G.kv(1, 1.1, 24_000_000, 10**7, seed=12)
+    q = {"cols": [k, v], "keys": [0], "preds": [], "aggs": [("count", 1, [])]}
+    plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT)
+    assert plan.est_groups == np.unique(k.cpu().numpy()).size
