@@ -250,29 +250,56 @@ class Clocks:
 
 # ------------------------------------------------------------ CPU (oracle)
 
-def time_oracle_parts(inp, sz, frac_rows):
-    """Time the oracle on row prefixes; returns {part: (rows, seconds)}."""
+def time_oracle_parts(inp, sz, frac_rows, threads: int = 1):
+    """Time the oracle on row prefixes; returns {part: (rows, seconds)}.
+    threads > 1: the oracle on hash partitions of the rows, one thread each
+    (oracle.partitioned; results left in partition order)."""
     import oracle
 
+    if threads > 1:
+        from oracle import partitioned
+
+        groupby = lambda q: partitioned.groupby(q, threads=threads, sort=False)
+        join = lambda b, y, p: partitioned.join(b, y, p, threads=threads, sort=False)
+    else:
+        groupby, join = oracle.groupby, oracle.join
     out = {}
     n = max(1, int(sz["li"] * frac_rows["lineitem"]))
     q = dict(inp["li"])
     q["cols"] = [c[:n] for c in q["cols"]]
     t = time.perf_counter()
-    oracle.groupby(q)
+    groupby(q)
     out["lineitem"] = (n, time.perf_counter() - t)
     npr = max(1, int(sz["np"] * frac_rows["join"]))
     t = time.perf_counter()
-    oracle.join(inp["bk"], inp["bp"], inp["pk"][:npr])
+    join(inp["bk"], inp["bp"], inp["pk"][:npr])
     out["join"] = (sz["nb"] + npr, time.perf_counter() - t)
     for name, key in (("zipf", "zipf"), ("fourkeys", "four")):
         n = max(1, int(sz["big"] * frac_rows[name]))
         q = dict(inp[key])
         q["cols"] = [c[:n] for c in q["cols"]]
         t = time.perf_counter()
-        oracle.groupby(q)
+        groupby(q)
         out[name] = (n, time.perf_counter() - t)
     return out
+
+
+def cpu_partitioned(inp, sz, rows_full, fracs):
+    """The multi-core CPU figure: the oracle per hash partition on every host
+    core, on the same row prefixes as the single-core baseline.  A failure is
+    reported in the line, not raised (it is context, not the measurement)."""
+    try:
+        from oracle import partitioned
+
+        threads = partitioned.default_threads()
+        t = time_oracle_parts(inp, sz, fracs, threads=threads)
+        v, _ = extrapolate(t, rows_full)
+        parts = {p: r / s for p, (r, s) in t.items()}
+        return {"value": v, "unit": "rows/s", "cores": threads,
+                "kind": "oracle per hash partition, one thread each",
+                "sample": sample_text(fracs, sz), "parts_rows_per_s": parts}
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def extrapolate(timings, rows_full):
@@ -488,6 +515,7 @@ def main():
         v, _ = extrapolate(t, rows_full)
         line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
                                 "sample": sample_text(CPU_FRACS, sz)}
+        line["cpu_partitioned"] = cpu_partitioned(inp, sz, rows_full, CPU_FRACS)
     if rank == 0 and args.learned > 0:
         line["learned"] = run_learned(args)
     if rank == 0 and not args.no_batched:

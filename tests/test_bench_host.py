@@ -78,3 +78,26 @@ def test_capture_void_when_launch_host_code_changes(tmp_path, monkeypatch):
     assert bench.captured("gb_main_keyset", "zipf", sz) == (None, None)
     host.unlink()
     assert bench.captured("gb_main_keyset", "zipf", sz) == (None, None)
+
+
+def test_cpu_legs_single_and_partitioned(monkeypatch):
+    sz = dict(li=3000, nb=1000, np=6000, big=20_000)
+    inp = bench.make_inputs(sz, seed=0)
+    fr = {"lineitem": 1.0, "join": 0.5, "zipf": 0.5, "fourkeys": 0.5}
+    one = bench.time_oracle_parts(inp, sz, fr)
+    many = bench.time_oracle_parts(inp, sz, fr, threads=3)
+    assert one.keys() == many.keys() == set(bench.PARTS)
+    assert all(one[p][0] == many[p][0] and many[p][1] > 0 for p in one)
+    rows_full = bench.part_rows(sz)
+    line = bench.cpu_partitioned(inp, sz, rows_full, fr)
+    assert line["value"] > 0 and line["cores"] >= 1 and line["unit"] == "rows/s"
+    assert set(line["parts_rows_per_s"]) == set(bench.PARTS)
+
+    from oracle import partitioned
+
+    def boom(*a, **k):
+        raise RuntimeError("planted")
+
+    monkeypatch.setattr(partitioned, "groupby", boom)
+    monkeypatch.setattr(partitioned, "default_threads", lambda: 2)
+    assert bench.cpu_partitioned(inp, sz, rows_full, fr) == {"error": "RuntimeError: planted"}
