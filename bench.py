@@ -191,8 +191,34 @@ def captured(kernel, part, sz):
         src = os.path.join(ROOT, rel_path)
         if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != digest:
             return None, None
-    units = {"lineitem": sz["li"], "join": sz["np"], "zipf": sz["big"], "fourkeys": sz["big"]}[part]
+    units = launch_units(part, sz)
     return k["bytes_per_unit"] * units, k.get("warp_inst_per_unit", 0.0) * units or None
+
+
+def launch_units(part, sz):
+    """Rows (probe rows for the join) one launch of the part's hot kernel covers."""
+    return {"lineitem": sz["li"], "join": sz["np"], "zipf": sz["big"], "fourkeys": sz["big"]}[part]
+
+
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
+
+
+def kernel_table(kern, inp, res, peak_gbs):
+    """Per (part, kernel): launches, total ms, share of kernel time and, where
+    the kernel has algorithmic bytes, their rate and its fraction of peak_gbs."""
+    total = sum(v[1] for v in kern.values()) or 1.0
+    out = {}
+    for (p, k), (n, ms) in sorted(kern.items(), key=lambda kv: -kv[1][1]):
+        d = {"launches": n, "total_ms": ms, "share": ms / total}
+        try:
+            b = algo_bytes(k, p, inp, res)
+        except (KeyError, IndexError, TypeError):
+            b = 0
+        if b and n and ms > 0:
+            d["algo_gbs"] = b / (ms / n / 1e3) / 1e9
+            d["frac"] = d["algo_gbs"] / peak_gbs
+        out[f"{p}/{k}"] = d
+    return out
 
 
 # ----------------------------------------------------------------- clocks
@@ -465,7 +491,6 @@ def main():
         d["rows"] = rows_full[p]
         d["rows_per_s"] = rows_full[p] / (d["ms"] / 1e3)
         d["launches"] //= args.steps
-    total_kms = sum(v[1] for v in kern.values()) or 1.0
     (dp, dk), (dn, dms) = max(kern.items(), key=lambda kv: kv[1][1])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -476,8 +501,7 @@ def main():
     abytes = algo_bytes(dk, dp, inp, g.results)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
     traffic, winst = captured(dk, dp, sz)
-    kernels = {f"{p}/{k}": {"launches": v[0], "total_ms": v[1], "share": v[1] / total_kms}
-               for (p, k), v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+    kernels = kernel_table(kern, inp, g.results, peak_gbs)
     clocks = clk.summary()
 
     line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world,
@@ -491,7 +515,9 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs, "traffic": traffic,
                          "kernel": f"{dp}/{dk}", "algo_bytes_per_launch": abytes,
-                         "ms_per_launch": per_launch_ms, "peak_source": peak_src},
+                         "ms_per_launch": per_launch_ms, "peak_source": peak_src,
+                         "peak_nominal": NOMINAL_HBM_GBS,
+                         "frac_nominal": achieved / NOMINAL_HBM_GBS},
             "gpu_launches": launches, "kernels": kernels, "clocks": clocks}
     # the paper's instruction roofline (Sec. 2.2): warp instructions per second
     # against N_SM x 4 schedulers x the SM clock sampled during the run, and
@@ -505,6 +531,7 @@ def main():
             "kernel": f"{dp}/{dk}", "achieved_warp_inst_per_s": inst_rate,
             "peak_warp_inst_per_s": issue_peak, "frac": inst_rate / issue_peak,
             "warp_inst_per_sector": winst / (traffic / 32) if traffic else None,
+            "warp_inst_per_row": winst / launch_units(dp, sz),
             "ridge_inst_per_sector": issue_peak / (peak_gbs * 1e9 / 32),
             "n_sm": sms, "sm_mhz": clocks["sm_mhz"], "source": "profiles/kernel_traffic.txt"}
 

@@ -101,3 +101,29 @@ def test_cpu_legs_single_and_partitioned(monkeypatch):
     monkeypatch.setattr(partitioned, "groupby", boom)
     monkeypatch.setattr(partitioned, "default_threads", lambda: 2)
     assert bench.cpu_partitioned(inp, sz, rows_full, fr) == {"error": "RuntimeError: planted"}
+
+
+def test_kernel_table_rates_and_shares():
+    inp = _inp()
+    res = {"zipf": (_T(7), [_T(7)] * 4), "join": (_T(900), _T(900), _T(900)),
+           "zipf.records": 600}
+    kern = {("zipf", "gb_main_keyset"): [2, 4.0], ("zipf", "sketch"): [1, 1.0],
+            ("join", "join_probe"): [1, 0.5], ("zipf", "gb_part_scan"): [2, 0.0]}
+    t = bench.kernel_table(kern, inp, res, peak_gbs=1.0)
+    assert list(t) == ["zipf/gb_main_keyset", "zipf/sketch", "join/join_probe", "zipf/gb_part_scan"]
+    assert abs(sum(d["share"] for d in t.values()) - 1.0) < 1e-12
+    # 8000 B per launch in 2 ms
+    assert abs(t["zipf/gb_main_keyset"]["algo_gbs"] - 8000 / 2e-3 / 1e9) < 1e-12
+    assert t["zipf/gb_main_keyset"]["frac"] == t["zipf/gb_main_keyset"]["algo_gbs"]
+    assert "algo_gbs" not in t["zipf/sketch"] and "algo_gbs" not in t["zipf/gb_part_scan"]
+    assert abs(t["join/join_probe"]["algo_gbs"] - (8000 + 900 * 16) / 0.5e-3 / 1e9) < 1e-12
+    # a kernel whose bytes cannot be derived keeps its timing only
+    t = bench.kernel_table({("join", "gb_compact"): [1, 1.0]}, inp, {}, 1.0)
+    assert t["join/gb_compact"] == {"launches": 1, "total_ms": 1.0, "share": 1.0}
+
+
+def test_launch_units():
+    sz = bench.full_sizes(False)
+    assert bench.launch_units("zipf", sz) == 200_000_000
+    assert bench.launch_units("join", sz) == 16_000_000
+    assert bench.launch_units("lineitem", sz) == 1_000_000
