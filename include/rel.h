@@ -167,7 +167,9 @@ typedef struct {
  *    groups_hint > 0: size the table for that many groups (no GPU work);
  *    flags & REL_PLAN_EXACT: count distinct qualifying keys on the GPU; needs
  *      plan->scratch_bytes of ws (query with ws = NULL: returns
- *      REL_E_CAPACITY after filling scratch_bytes);
+ *      REL_E_CAPACITY after filling scratch_bytes).  The count first uses a
+ *      key set of at most 2^24 slots and reads the keys a second time, into
+ *      the full set, only when the distinct keys overflow it;
  *    otherwise: size for n_rows groups (always sufficient, rarely economical).
  *    flags & REL_PLAN_LEARNED (without a hint or REL_PLAN_EXACT): run
  *      rel_sketch, then the registered planner network (rel_planner_set) on
