@@ -334,7 +334,7 @@ def extrapolate(timings, rows_full):
     return sum(rows_full.values()) / secs, secs
 
 
-CPU_FRACS = {"lineitem": 1.0, "join": 0.125, "zipf": 0.05, "fourkeys": 0.05}
+CPU_FRACS = {"lineitem": 1.0, "join": 0.5, "zipf": 0.25, "fourkeys": 0.25}
 REF_FRACS = {"lineitem": 0.2, "join": 0.0625, "zipf": 0.01, "fourkeys": 0.01}
 
 
@@ -541,7 +541,9 @@ def main():
         t = time_oracle_parts(inp, sz, CPU_FRACS)
         v, _ = extrapolate(t, rows_full)
         line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                                "sample": sample_text(CPU_FRACS, sz)}
+                                "sample": sample_text(CPU_FRACS, sz),
+                                "parts_rows_per_s": {p: r / s for p, (r, s) in t.items()},
+                                "sample_s": sum(s for _, s in t.values())}
         line["cpu_partitioned"] = cpu_partitioned(inp, sz, rows_full, CPU_FRACS)
     if rank == 0 and args.learned > 0:
         line["learned"] = run_learned(args)
