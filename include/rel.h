@@ -291,10 +291,13 @@ rel_status rel_sketch_batched(const rel_groupby_desc* descs, int32_t n, void* ws
  * the number of groups.  max_groups outside 1..REL_STATIC_MAX_GROUPS is
  * rejected with REL_E_UNSUPPORTED before any device work; more groups than
  * the table sized from max_groups can hold gives REL_E_OVERFLOW.
+ * n_groups_host is required here (NULL gives REL_E_INVALID): the call syncs
+ * the stream, writes the group count there and reads the overflow flag.
  *
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array:
+ * Every call looks up the scratch array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device may load the
+ * library's device code, so make it before any stream capture.  Every call
+ * on a device shares the one array:
  * each call clears what it uses before its kernels run, so sequential calls
  * are independent, but calls that overlap on the GPU (different streams or
  * threads without ordering between them) race and give wrong results. */
@@ -302,6 +305,34 @@ rel_status rel_sketch_batched(const rel_groupby_desc* descs, int32_t n, void* ws
 rel_status rel_groupby_agg_static(const rel_groupby_desc* desc, int64_t max_groups,
                                   int64_t* out_keys, int64_t* const* out_aggs,
                                   int64_t out_capacity, int64_t* n_groups_host, void* stream);
+
+/* The learned sizing rule, on the host: from a sketch and the planner
+ * network's 4 outputs y (host floats: log2 of the group count, then the
+ * logits of REL_VAR_SMEM, REL_VAR_GLOBAL, REL_VAR_PARTITIONED) to the
+ * estimate and variant REL_PLAN_LEARNED uses.  est_groups = the smaller of
+ * n_rows and ceil(1.25 * 2^(clamp(y0, 0, 61) + 1)) (n_rows when y0 is not
+ * finite), raised to the sample's distinct keys (info->ndv); variant = the
+ * largest logit among the allowed variants (REL_VAR_PARTITIONED only when
+ * partitioned_ok), ties to the lower-numbered one.  The paper has no planner;
+ * this is the decision rule of the learned form built on its operators.
+ * No device work.  Returns REL_OK or REL_E_INVALID (NULL pointers, n_rows < 0). */
+rel_status rel_plan_learned_rule(const rel_sketch_info* info, const float* y, int64_t n_rows,
+                                 int32_t partitioned_ok, int64_t* est_groups, int32_t* variant);
+
+/* Learned plans for n group-bys at once (the batched mode's sizing step):
+ * one rel_sketch_batched launch, one network forward over all n feature
+ * rows, then rel_plan_learned_rule per input with the variant chosen among
+ * REL_VAR_SMEM and REL_VAR_GLOBAL (the batched launch has no partitioned
+ * variant).  flags: REL_PLAN_LEARNED, optionally | REL_PLAN_SKETCH (pin the
+ * sample's heavy hitters as rel_plan_size does); anything else gives
+ * REL_E_UNSUPPORTED.  descs: n host descriptors; plans: n host plans,
+ * filled as rel_plan_size fills them.  ws: rel_plan_size_batched_ws_bytes(n)
+ * device bytes.  Syncs the stream.  Returns REL_OK, REL_E_INVALID (bad
+ * descriptor, no registered network), REL_E_CAPACITY (ws too small),
+ * REL_E_UNSUPPORTED, REL_E_CUDA. */
+uint64_t rel_plan_size_batched_ws_bytes(int32_t n);
+rel_status rel_plan_size_batched(const rel_groupby_desc* descs, int32_t n, uint32_t flags,
+                                 void* ws, size_t ws_bytes, rel_plan* plans, void* stream);
 
 /* ---------------------------------------------------- planner network */
 

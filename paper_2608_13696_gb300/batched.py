@@ -11,8 +11,6 @@ their own (the planner's fallback).
 """
 from __future__ import annotations
 
-import ctypes
-import math
 import time
 
 import numpy as np
@@ -27,38 +25,30 @@ def kv_query(keys: torch.Tensor, vals: torch.Tensor, ops=GB_OPS) -> dict:
     return {"cols": [keys, vals], "keys": [0], "preds": [], "aggs": [(op, 1, []) for op in ops]}
 
 
-def next_pow2(x: int) -> int:
-    p = 1
-    while p < x:
-        p <<= 1
-    return p
-
-
 def learned_sizes(gb_inputs, planner_params: torch.Tensor | None = None):
-    """Per group-by (est_groups, slots, variant) from the batched sketch and
-    one batched network forward (the registered planner's parameters)."""
+    """Per group-by (est_groups, slots, variant) from the library's batched
+    learned planning (rel_plan_size_batched: one sketch launch, one network
+    launch, the learned sizing rule).  planner_params: FP32 network
+    parameters to use instead of the registered ones (registered for the
+    call, then the previous network is put back)."""
     if not gb_inputs:
         return []
-    infos = rel.sketch_kv_batched([k for k, _ in gb_inputs], [v for _, v in gb_inputs])
-    dev = gb_inputs[0][0].device
-    feats = np.empty((len(infos), rel.MLP_IN), dtype=np.float32)
-    for i, s in enumerate(infos):
-        ctypes.memmove(feats[i].ctypes.data, ctypes.addressof(s.features), 4 * rel.MLP_IN)
-    x = torch.from_numpy(feats).to(dev)
-    p = planner_params if planner_params is not None else rel._planner_ref[0]
-    bf = torch.empty(rel.MLP_PARAMS, dtype=torch.bfloat16, device=dev)
-    rel.mlp_round(p, bf)
-    y = rel.mlp_forward(bf, p, x).cpu().numpy()
-    out = []
-    for (k, _), s, yi in zip(gb_inputs, infos, y):
-        n = k.numel()
-        est = n
-        if math.isfinite(yi[0]):  # the library's learned sizing rule (2x + 25 % headroom)
-            est = min(n, math.ceil(2.0 ** (min(max(float(yi[0]), 0.0), 61.0) + 1.0) * 1.25))
-        est = max(est, int(s.ndv))
-        variant = 1 + int(np.argmax(yi[1:3]))  # per-CTA tables or global table
-        out.append((est, next_pow2(max(16, 2 * est)), variant))
-    return out
+    keys = [k for k, _ in gb_inputs]
+    vals = [v for _, v in gb_inputs]
+    if planner_params is None:
+        plans = rel.plan_kv_batched(keys, vals, GB_OPS)
+    else:
+        prev = rel._planner_ref
+        rel.planner_set(planner_params)
+        try:
+            plans = rel.plan_kv_batched(keys, vals, GB_OPS)
+        finally:
+            if prev is None:
+                rel.planner_set(None)
+            else:
+                rel._planner_ref = prev
+                rel.load().rel_planner_set(prev[1].data_ptr(), prev[0].data_ptr())
+    return [(p.est_groups, p.slots, p.variant) for p in plans]
 
 
 def make_batch(gb_inputs, join_inputs, sizes) -> rel.Batch:

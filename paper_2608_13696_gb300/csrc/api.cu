@@ -707,6 +707,29 @@ constexpr uint64_t LEARN_SCRATCH = 2048;
 constexpr uint64_t LEARN_OUT_OFF = 1280;
 constexpr double LEARN_LOG2_MARGIN = 1.0;  // sizing headroom over the network's log2 estimate
 
+// The learned sizing rule: from the network's outputs y (log2 of the group
+// count, then the logits of the three variants) to an estimate and a
+// variant.  Twice the predicted count plus 25 %: an underestimate costs a
+// wasted run and the exact pre-pass, an overestimate only a larger table;
+// never below the distinct keys already seen in the sample, never above the
+// rows.  The variant is the most likely one among those allowed (ties go to
+// the lower-numbered variant).
+void learned_rule(const rel_sketch_info& info, const float* y, int64_t n_rows, bool p_ok,
+                  int64_t* est, int* variant) {
+  int64_t n = n_rows;
+  if (std::isfinite(y[0])) {
+    const double y0 = std::min(std::max((double)y[0], 0.0), 61.0) + LEARN_LOG2_MARGIN;
+    const double g = std::ceil(std::exp2(y0) * 1.25);
+    n = g < (double)n_rows ? (int64_t)g : n_rows;
+  }
+  if (n < info.ndv) n = info.ndv;
+  *est = n;
+  int best = REL_VAR_SMEM;
+  for (int v = REL_VAR_GLOBAL; v <= REL_VAR_PARTITIONED; ++v)
+    if ((v != REL_VAR_PARTITIONED || p_ok) && y[v] > y[best]) best = v;
+  *variant = best;
+}
+
 // The learned sizing step: sketch, network forward, estimate and variant.
 rel_status learned_estimate(const rel_groupby_desc* d, bool p_ok, void* ws, size_t ws_bytes,
                             rel_sketch_info* info, int64_t* est, int* variant, cudaStream_t st) {
@@ -724,22 +747,15 @@ rel_status learned_estimate(const rel_groupby_desc* d, bool p_ok, void* ws, size
   e = cudaMemcpyAsync(y, dy, sizeof y, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the planner output");
-  // twice the predicted count plus 25 %: an underestimate costs a wasted run
-  // and the exact pre-pass, an overestimate only a larger table; never below
-  // the distinct keys already seen in the sample, never above the rows
-  int64_t n = d->n_rows;
-  if (std::isfinite(y[0])) {
-    const double y0 = std::min(std::max((double)y[0], 0.0), 61.0) + LEARN_LOG2_MARGIN;
-    const double g = std::ceil(std::exp2(y0) * 1.25);
-    n = g < (double)d->n_rows ? (int64_t)g : d->n_rows;
-  }
-  if (n < info->ndv) n = info->ndv;
-  *est = n;
-  int best = REL_VAR_SMEM;
-  for (int v = REL_VAR_GLOBAL; v <= REL_VAR_PARTITIONED; ++v)
-    if ((v != REL_VAR_PARTITIONED || p_ok) && y[v] > y[best]) best = v;
-  *variant = best;
+  learned_rule(*info, y, d->n_rows, p_ok, est, variant);
   return REL_OK;
+}
+
+// Workspace of rel_plan_size_batched: the batched sketch's, then the feature
+// rows, then the network outputs.
+uint64_t batched_plan_feat_off(int32_t n) { return align_up(rel_sketch_batched_ws_bytes(n), 256); }
+uint64_t batched_plan_out_off(int32_t n) {
+  return batched_plan_feat_off(n) + align_up(4ull * REL_MLP_IN * (uint64_t)(n > 0 ? n : 1), 256);
 }
 
 // Table layers for a variant (0 = the rule by group count).
@@ -1173,6 +1189,76 @@ rel_status rel_sketch_batched(const rel_groupby_desc* descs, int32_t n, void* ws
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the sketches");
   for (int i = 0; i < n; ++i) sketch_fill(descs + i, h[i], bits[i], out + i);
+  return REL_OK;
+}
+
+rel_status rel_plan_learned_rule(const rel_sketch_info* info, const float* y, int64_t n_rows,
+                                 int32_t partitioned_ok, int64_t* est_groups, int32_t* variant) {
+  if (!info || !y || !est_groups || !variant)
+    return set_error("plan: NULL argument to the learned rule"), REL_E_INVALID;
+  if (n_rows < 0) return set_error("plan: n_rows < 0"), REL_E_INVALID;
+  int64_t est = 0;
+  int v = REL_VAR_SMEM;
+  learned_rule(*info, y, n_rows, partitioned_ok != 0, &est, &v);
+  *est_groups = est;
+  *variant = v;
+  return REL_OK;
+}
+
+uint64_t rel_plan_size_batched_ws_bytes(int32_t n) {
+  if (n < 0) return 0;
+  return batched_plan_out_off(n) + align_up(4ull * REL_MLP_OUT * (uint64_t)(n > 0 ? n : 1), 256);
+}
+
+rel_status rel_plan_size_batched(const rel_groupby_desc* descs, int32_t n, uint32_t flags,
+                                 void* ws, size_t ws_bytes, rel_plan* plans, void* stream) {
+  if (n < 0 || (n > 0 && (!descs || !plans)))
+    return set_error("plan: bad batched arguments"), REL_E_INVALID;
+  if (!(flags & REL_PLAN_LEARNED) || (flags & (REL_PLAN_EXACT | REL_PLAN_GENERIC | REL_PLAN_FORCE_MASK)))
+    return set_error("plan: batched planning is the learned form (REL_PLAN_LEARNED, optionally "
+                     "REL_PLAN_SKETCH) only"),
+           REL_E_UNSUPPORTED;
+  if (n == 0) return REL_OK;
+  rel_status r;
+  for (int i = 0; i < n; ++i)
+    if ((r = validate_desc(descs + i))) return r;
+  if (!g_planner_bf16) return set_error("plan: no planner network registered"), REL_E_INVALID;
+  const uint64_t need = rel_plan_size_batched_ws_bytes(n);
+  if (!ws || ws_bytes < need)
+    return set_error("plan: batched planning needs %llu workspace bytes", (unsigned long long)need),
+           REL_E_CAPACITY;
+  cudaStream_t st = as_stream(stream);
+  std::vector<rel_sketch_info> info(n);
+  if ((r = rel_sketch_batched(descs, n, ws, batched_plan_feat_off(n), info.data(), stream)))
+    return r;
+  std::vector<float> x((size_t)n * REL_MLP_IN), y((size_t)n * REL_MLP_OUT);
+  for (int i = 0; i < n; ++i)
+    std::memcpy(&x[(size_t)i * REL_MLP_IN], info[i].features, sizeof(float) * REL_MLP_IN);
+  float* dx = (float*)((uint8_t*)ws + batched_plan_feat_off(n));
+  float* dy = (float*)((uint8_t*)ws + batched_plan_out_off(n));
+  cudaError_t e = cudaMemcpyAsync(dx, x.data(), sizeof(float) * x.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemcpyAsync");
+  if ((r = mlp_forward(g_planner_bf16, g_planner_f32, dx, n, dy, nullptr, st))) return r;
+  e = cudaMemcpyAsync(y.data(), dy, sizeof(float) * y.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "reading the planner outputs");
+  for (int i = 0; i < n; ++i) {
+    const rel_groupby_desc* d = descs + i;
+    rel_plan* plan = plans + i;
+    std::memset(plan, 0, sizeof *plan);
+    plan->flags = flags;
+    GbParams p;
+    const Mapped m = match_shape(d, p);
+    int64_t est = 0;
+    int variant = REL_VAR_SMEM;
+    // the batched launch has no partitioned variant
+    learned_rule(info[i], &y[(size_t)i * REL_MLP_OUT], d->n_rows, false, &est, &variant);
+    plan->est_groups = est;
+    plan->slots = (int64_t)next_pow2((uint64_t)(2 * est < 16 ? 16 : 2 * est));
+    choose_variant(variant, est, d->n_rows, gb_shape_width(m.shape), false, plan);
+    plan->workspace_bytes = plan_ws_bytes(plan, d->n_aggs, d->n_rows);
+    if (flags & REL_PLAN_SKETCH) apply_sketch(info[i], gb_shape_width(m.shape), plan);
+  }
   return REL_OK;
 }
 

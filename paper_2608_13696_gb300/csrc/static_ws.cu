@@ -13,12 +13,10 @@
 // The array is a file-scope __device__ variable: every GPU on which the
 // library is loaded holds its STATIC_WS_BYTES (about 4.5 MiB) until the
 // process exits.  Host code must not hand the array's name to a kernel -- on
-// the host that name is only a stand-in, not a device address -- so the
-// first call on each device looks up the device address with
-// cudaGetSymbolAddress (with that device current) and every later call on
-// that device reuses it.
-#include <mutex>
-
+// the host that name is only a stand-in, not a device address -- so every
+// call looks up the device address with cudaGetSymbolAddress, with the
+// caller's device current.  The lookup is cheap next to the kernels, and a
+// fresh one stays valid after a cudaDeviceReset reloaded the module.
 #include "rel_internal.cuh"
 
 namespace {
@@ -31,27 +29,12 @@ constexpr size_t STATIC_WS_BYTES =
 // Workspace shared by every call on a device: header, keys, aggregate words.
 static __device__ __align__(256) unsigned char g_static_ws[STATIC_WS_BYTES];
 
-constexpr int MAX_DEVICES = 128;
-std::mutex g_mu;
-void* g_ws_addr[MAX_DEVICES] = {};
-
-// Device address of g_static_ws on the current device (set up once per device).
+// Device address of g_static_ws on the current device.
 rel_status static_ws_address(void** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= MAX_DEVICES) {
-    relhost::set_error("static group-by: device %d outside 0..%d", dev, MAX_DEVICES - 1);
-    return REL_E_UNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ws_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_ws);
-    if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-    g_ws_addr[dev] = p;
-  }
-  *out = g_ws_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+  *out = p;
   return REL_OK;
 }
 
@@ -67,6 +50,14 @@ extern "C" rel_status rel_groupby_agg_static(const rel_groupby_desc* desc, int64
         "%zu-byte scratch table holds; use rel_groupby_agg with a caller workspace",
         (long long)max_groups, (long long)STATIC_MAX_GROUPS, STATIC_WS_BYTES);
     return REL_E_UNSUPPORTED;
+  }
+  // Overflow of the fixed table is only detected by reading the status back,
+  // which needs the host count: without it a caller could get a truncated
+  // result reported as success.
+  if (!n_groups_host) {
+    relhost::set_error("static group-by: n_groups_host must not be NULL (it carries the "
+                       "group count and the overflow check)");
+    return REL_E_INVALID;
   }
   // Host-only sizing: a positive hint makes rel_plan_size touch no device.
   rel_plan plan;

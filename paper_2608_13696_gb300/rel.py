@@ -188,7 +188,8 @@ EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join
            "rel_groupby_auto", "rel_groupby_auto_ws_bytes", "rel_mlp_round", "rel_mlp_forward",
            "rel_mlp_ws_bytes", "rel_mlp_backward", "rel_mlp_adamw", "rel_planner_set",
            "rel_batch_ws_bytes", "rel_batch_prepare", "rel_batch_run", "rel_batch_results",
-           "rel_batch_autotune", "rel_sketch_batched", "rel_sketch_batched_ws_bytes"]
+           "rel_batch_autotune", "rel_sketch_batched", "rel_sketch_batched_ws_bytes",
+           "rel_plan_learned_rule", "rel_plan_size_batched", "rel_plan_size_batched_ws_bytes"]
 SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
 
@@ -273,6 +274,14 @@ def load(build_if_stale: bool = True):
         L.rel_sketch_batched.restype = i32
         L.rel_sketch_batched.argtypes = [ctypes.POINTER(GroupByDesc), i32, vp, ctypes.c_size_t,
                                          ctypes.POINTER(SketchInfo), vp]
+        L.rel_plan_learned_rule.restype = i32
+        L.rel_plan_learned_rule.argtypes = [ctypes.POINTER(SketchInfo), vp, i64, i32,
+                                            ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.rel_plan_size_batched_ws_bytes.restype = u64
+        L.rel_plan_size_batched_ws_bytes.argtypes = [i32]
+        L.rel_plan_size_batched.restype = i32
+        L.rel_plan_size_batched.argtypes = [ctypes.POINTER(GroupByDesc), i32, u32, vp,
+                                            ctypes.c_size_t, ctypes.POINTER(Plan), vp]
         PG, PJ = ctypes.POINTER(BatchGroupBy), ctypes.POINTER(BatchJoinC)
         PC, PH = ctypes.POINTER(BatchConfig), ctypes.POINTER(BatchHandle)
         L.rel_batch_ws_bytes.restype = u64
@@ -550,13 +559,10 @@ def sketch_batched(qs: list, stream=None) -> list:
     return list(out)
 
 
-def sketch_kv_batched(keys: list, vals: list, ops=("sum", "count"), stream=None) -> list:
-    """sketch_batched for key/value inputs (one int32/int64 key column, one
-    int64 value column), descriptors built column-wise."""
-    L = load()
+def _kv_descs(keys: list, vals: list, ops):
+    """Key/value descriptors (one int32/int64 key column, one int64 value
+    column) built column-wise; returns (ctypes array, objects to keep alive)."""
     n = len(keys)
-    if n == 0:
-        return []
     cols = np.zeros(2 * n, dtype=_np_dtype(Col))
     cols["data"][0::2] = [k.data_ptr() for k in keys]
     cols["type"][0::2] = [_DT[k.dtype] for k in keys]
@@ -572,10 +578,50 @@ def sketch_kv_batched(keys: list, vals: list, ops=("sum", "count"), stream=None)
     d["preds"] = 0
     d["aggs"] = ctypes.addressof(aggs)
     arr = (GroupByDesc * n).from_buffer(d)
+    return arr, (cols, kc, aggs, d)
+
+
+def sketch_kv_batched(keys: list, vals: list, ops=("sum", "count"), stream=None) -> list:
+    """sketch_batched for key/value inputs (one int32/int64 key column, one
+    int64 value column), descriptors built column-wise."""
+    L = load()
+    n = len(keys)
+    if n == 0:
+        return []
+    arr, keep = _kv_descs(keys, vals, ops)
     ws = _ws(L.rel_sketch_batched_ws_bytes(n), keys[0].device)
     out = (SketchInfo * n)()
     _check(L.rel_sketch_batched(arr, n, ws.data_ptr(), ws.numel(), out, _stream(stream)))
     return list(out)
+
+
+def plan_kv_batched(keys: list, vals: list, ops=("sum", "count"), flags: int = PLAN_LEARNED,
+                    stream=None) -> list:
+    """rel_plan_size_batched for key/value inputs: learned plans of all of
+    them from one sketch launch and one network launch (the registered
+    network)."""
+    L = load()
+    n = len(keys)
+    if n == 0:
+        return []
+    arr, keep = _kv_descs(keys, vals, ops)
+    ws = _ws(L.rel_plan_size_batched_ws_bytes(n), keys[0].device)
+    plans = (Plan * n)()
+    _check(L.rel_plan_size_batched(arr, n, flags, ws.data_ptr(), ws.numel(), plans,
+                                   _stream(stream)))
+    return list(plans)
+
+
+def plan_learned_rule(info: "SketchInfo", y, n_rows: int, partitioned_ok: bool = True):
+    """rel_plan_learned_rule (host only): (est_groups, variant) from a sketch
+    and the network's 4 outputs."""
+    L = load()
+    yy = np.ascontiguousarray(np.asarray(y, dtype=np.float32)[:MLP_OUT])
+    est, var = ctypes.c_int64(), ctypes.c_int32()
+    _check(L.rel_plan_learned_rule(ctypes.byref(info), yy.ctypes.data, n_rows,
+                                   1 if partitioned_ok else 0, ctypes.byref(est),
+                                   ctypes.byref(var)))
+    return est.value, var.value
 
 
 class JoinTable:

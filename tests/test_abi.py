@@ -135,6 +135,62 @@ def test_groupby_agg_argument_checks(L):
                              ctypes.byref(n), None) == rel.REL_E_CAPACITY
 
 
+def test_static_groupby_checks_before_any_device_work(L):
+    d, keep = _desc()
+    n = ctypes.c_int64()
+    out = (ctypes.c_void_p * 1)(0x3000)
+    # max_groups outside 1..REL_STATIC_MAX_GROUPS
+    for bad in (0, rel.STATIC_MAX_GROUPS + 1):
+        assert L.rel_groupby_agg_static(ctypes.byref(d), bad, 0x3000, out, 10, ctypes.byref(n),
+                                        None) == rel.REL_E_UNSUPPORTED
+        assert b"max_groups" in L.rel_last_error()
+    # the host count carries the overflow check: NULL is refused
+    assert L.rel_groupby_agg_static(ctypes.byref(d), 16, 0x3000, out, 10, None,
+                                    None) == rel.REL_E_INVALID
+    assert b"n_groups_host" in L.rel_last_error()
+
+
+def test_learned_rule_on_synthetic_network_outputs(L):
+    """The learned sizing rule, host only: est = min(rows, ceil(1.25 * 2^(clamp(y0, 0, 61)
+    + 1))), never below the sample's distinct keys; variant = largest allowed logit."""
+    info = rel.SketchInfo()
+    info.ndv = 7
+    nan = float("nan")
+    cases = [  # (y, rows, partitioned_ok) -> (est, variant)
+        ((10.0, 1.0, 3.0, 2.0), 10**6, True, (2560, rel.VAR_GLOBAL)),
+        ((10.0, 1.0, 3.0, 4.0), 10**6, True, (2560, rel.VAR_PARTITIONED)),
+        ((10.0, 1.0, 3.0, 4.0), 10**6, False, (2560, rel.VAR_GLOBAL)),
+        ((10.0, 2.0, 2.0, 2.0), 10**6, True, (2560, rel.VAR_SMEM)),
+        ((-5.0, 0.0, 0.0, 0.0), 10**6, True, (7, rel.VAR_SMEM)),  # ceil(2.5) = 3 < ndv
+        ((0.5, 0.0, 0.0, 0.0), 10**6, True, (7, rel.VAR_SMEM)),   # ceil(1.25 * 2^1.5) = 4 -> ndv
+        ((3.0, 0.0, 0.0, 0.0), 10**6, True, (20, rel.VAR_SMEM)),  # 1.25 * 16
+        ((40.0, 0.0, 1.0, 0.0), 1000, True, (1000, rel.VAR_GLOBAL)),
+        ((nan, 0.0, 1.0, 0.0), 12345, True, (12345, rel.VAR_GLOBAL)),
+        ((100.0, 0.0, 0.0, 0.0), 1 << 62, True, (1 << 62, rel.VAR_SMEM)),  # clamp at 61: 1.25*2^62
+    ]
+    for y, rows, pok, want in cases:
+        got = rel.plan_learned_rule(info, y, rows, pok)
+        assert got == want, (y, rows, pok, got, want)
+    est, var = ctypes.c_int64(), ctypes.c_int32()
+    assert L.rel_plan_learned_rule(None, None, 10, 1, ctypes.byref(est),
+                                   ctypes.byref(var)) == rel.REL_E_INVALID
+
+
+def test_batched_plan_checks_before_any_device_work(L):
+    d, keep = _desc()
+    plans = (rel.Plan * 1)()
+    n1 = L.rel_plan_size_batched_ws_bytes(1)
+    assert L.rel_plan_size_batched_ws_bytes(100) > n1 >= L.rel_sketch_batched_ws_bytes(1)
+    assert L.rel_plan_size_batched(ctypes.byref(d), 1, rel.PLAN_EXACT, None, 0, plans,
+                                   None) == rel.REL_E_UNSUPPORTED
+    assert L.rel_plan_size_batched(ctypes.byref(d), 0, rel.PLAN_LEARNED, None, 0, plans,
+                                   None) == rel.REL_OK
+    L.rel_planner_set(None, None)
+    assert L.rel_plan_size_batched(ctypes.byref(d), 1, rel.PLAN_LEARNED, None, 0, plans,
+                                   None) == rel.REL_E_INVALID
+    assert b"network" in L.rel_last_error()
+
+
 def test_join_argument_checks(L):
     t = rel.JoinTableC()
     assert L.rel_join_build(None, None, -1, None, 0, ctypes.byref(t), None) == rel.REL_E_UNSUPPORTED

@@ -4,8 +4,8 @@ Every aggregate is exact int64, so the bar is bit-exact equality after
 sorting by key.  Each case runs through the C ABI in every per-CTA table mode
 (thread-private, CTA-shared, global) and with both the specialised and the
 descriptor-interpreting kernel, at sizes spanning several tiles plus a
-ragged tail, and at the full sizes the benchmark times (checked on sampled
-groups and on properties that hold at any size)."""
+ragged tail (the full-size cases, every group compared, are in
+test_fullsize_gpu.py)."""
 import numpy as np
 import pytest
 import torch
@@ -171,47 +171,7 @@ def test_overflow_is_reported_not_hung():
     assert k.numel() == len(np.unique(keys))
 
 
-# --------------------------------------------------------------- full sizes
-
-N_BIG = 200_000_000
-
-
-def _big_checks(keys, vals, plan_flags, sample_keys):
-    kc, vc = cuda(keys), cuda(vals)
-    q = {"cols": [kc, vc], "keys": [0], "preds": [],
-         "aggs": [("sum", 1, []), ("count", 1, []), ("min", 1, []), ("max", 1, [])]}
-    plan = rel.plan_groupby(q, flags=plan_flags)
-    gk, ga = rel.groupby(q, plan=plan)
-    torch.cuda.synchronize()
-    # properties at any size
-    assert int(ga[1].sum()) == N_BIG
-    assert int(ga[0].sum()) == int(vc.sum())
-    assert int(ga[2].min()) == int(vc.min()) and int(ga[3].max()) == int(vc.max())
-    assert torch.unique(gk).numel() == gk.numel() == plan.est_groups
-    # exact check of sampled groups against the oracle on their rows
-    sample = np.unique(np.concatenate([sample_keys, gk[:16].cpu().numpy()]))
-    rows = np.isin(keys, sample)
-    ek, ea = oracle.groupby(oracle.kv_query(keys[rows], vals[rows]))
-    k_np = gk.cpu().numpy()
-    pos = {int(x): i for i, x in enumerate(k_np)}
-    idx = np.array([pos[int(x)] for x in ek])
-    got = np.stack([a.cpu().numpy()[idx] for a in ga])
-    np.testing.assert_array_equal(got, ea)
-    return plan
-
-
-def test_full_size_zipf_200m():
-    keys, vals = synth.zipf_kv(N_BIG, seed=0)
-    sample = np.array([synth.mix64_signed(r) for r in (1, 2, 3, 10, 1000, 10**5, 10**6)])
-    plan = _big_checks(keys, vals, rel.PLAN_EXACT, sample)
-    assert plan.variant == rel.VAR_PARTITIONED
-
-
-def test_full_size_four_keys_200m():
-    keys, vals = synth.few_keys_kv(N_BIG, n_keys=4, seed=0)
-    sample = np.array([synth.mix64_signed(r) for r in (1, 2)])
-    plan = _big_checks(keys, vals, rel.PLAN_EXACT, sample)
-    assert plan.est_groups == 4 and plan.tiny_slots == 8
+# ------------------------------------------ the exact pre-pass's key sets
 
 
 @pytest.mark.parametrize("key_type,generic", [("int64", False), ("int32", False), ("int64", True)])

@@ -99,3 +99,16 @@ def test_batch_recipe_ranges_and_determinism():
     assert G.batch_recipe(0) == r and G.batch_recipe(1) != r
     seeds = [x["seed"] for x in r["groupby"]] + [x["seed"] for x in r["join"]]
     assert len(set(seeds)) == len(seeds)
+
+
+def test_planner_instances_span_the_range():
+    """The 32 planner-workload seeds the GPU oracle test checks
+    (test_workload_oracle_gpu.py) cover the workload: small and large
+    instances and every key family."""
+    import synth.gpu
+
+    insts = [synth.gpu.instance(s, rows_lo=1_000_000, rows_hi=50_000_000)
+             for s in range(3_000_000, 3_000_032)]
+    rows = [i["rows"] for i in insts]
+    assert min(rows) < 3_000_000 and max(rows) > 25_000_000
+    assert {i["family"] for i in insts} == {f[0] for f in synth.gpu.FAMILIES}

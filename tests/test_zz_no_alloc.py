@@ -37,6 +37,9 @@ def test_two_calls_in_a_row_match_workspace_entry_point():
         assert len(rk) > 0
         np.testing.assert_array_equal(gk, rk)
         np.testing.assert_array_equal(ga, ra)
+        ek, ea = oracle.groupby(q)
+        np.testing.assert_array_equal(gk, ek)
+        np.testing.assert_array_equal(ga, ea)
 
 
 def test_repeated_call_sees_no_stale_state():
@@ -46,6 +49,9 @@ def test_repeated_call_sees_no_stale_state():
     second = canon_groupby(*rel.groupby_static(qc, max_groups=16))
     np.testing.assert_array_equal(first[0], second[0])
     np.testing.assert_array_equal(first[1], second[1])
+    ek, ea = oracle.groupby(oracle.kv_query(keys, vals))
+    np.testing.assert_array_equal(second[0], ek)
+    np.testing.assert_array_equal(second[1], ea)
 
 
 def test_sizes_beyond_the_maximum_are_rejected():
