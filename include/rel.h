@@ -130,6 +130,17 @@ typedef struct {
 /* Set in plan->flags by rel_groupby_auto when the first plan overflowed and
  * the call re-planned with the exact pre-pass. */
 #define REL_PLAN_FELL_BACK 0x10000u
+/* Test hook for the device-side wait limit, not for production use.  Set in
+ * plan->flags before rel_groupby_agg: the staged kernel's consumers never hand
+ * a shared-memory stage back to its producer, so once a CTA's ring has gone
+ * round once, the producer's bounded wait, and then the consumers', give up
+ * after 20 ms (instead of the normal 2 s); the producer still waits for the
+ * copies it issued, nothing is left in flight, and the call returns
+ * REL_E_TIMEOUT.  Only plans that run the staged kernel with a CTA that gets
+ * more tiles than stages (e.g. tile_rows = 256, n_stages = 2 on 10^6 rows)
+ * reach the wait; other plans run normally.  The paper has no counterpart:
+ * this tests the library's failure detection without faulting a GPU. */
+#define REL_PLAN_TEST_STALL 0x40000000u
 
 #define REL_MAX_HOT 32
 
@@ -485,7 +496,10 @@ typedef struct {
   int64_t n_probe;
 } rel_join_probe_desc;
 
-/* Device bytes rel_join_build needs for n_build build rows. */
+/* Device bytes rel_join_build needs for n_build build rows: a 256-byte
+ * header, next_pow2(2 * n_build) (at least 16) slots of 32 bytes (key,
+ * payload, build row index: one sector, read by the probe with one load), and
+ * a 16-byte side entry per build row for the key INT64_MIN. */
 uint64_t rel_join_ws_bytes(int64_t n_build);
 
 /* Build (the paper's insert step): every build row j (key[j], payload[j])

@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "distinct.cuh"
 #include "groupby.cuh"
 #include "join.cuh"
 #include "mlp.cuh"
@@ -249,6 +250,7 @@ Mapped match_shape(const rel_groupby_desc* d, GbParams& p) {
 // Kernel parameters of a descriptor, aggregates in the mapped order.
 void fill_params(const rel_groupby_desc* d, const int* perm, GbParams& p) {
   std::memset(&p, 0, sizeof p);
+  p.wait_ns = WAIT_LIMIT_NS;
   p.n_rows = d->n_rows;
   p.n_cols = d->n_cols;
   p.n_keys = d->n_keys;
@@ -699,8 +701,17 @@ void sketch_fill(const rel_groupby_desc* d, const DevSketch& h, int bits, rel_sk
 const void* g_planner_bf16 = nullptr;
 const float* g_planner_f32 = nullptr;
 
-// slots of the exact pre-pass's first key set (8 bytes each: 128 MB, L2-sized)
+// slots of the exact pre-pass's first key set in the staged kernel (8 bytes
+// each: 128 MB)
 constexpr uint64_t EXACT_SET_L2_SLOTS = 1ull << 24;
+// bytes of the streaming distinct count's first key set (and of each set of
+// its hash-split passes): at this size a key's home bucket is almost always
+// the only one probed, and the random bucket reads still mostly hit L2 while
+// the column streams past
+constexpr uint64_t EXACT_SET_FIRST_BYTES = 256ull << 20;
+// entries of the streaming distinct count's per-CTA filter (0: none; the
+// buckets of frequent keys are served by L1 instead)
+constexpr uint32_t EXACT_FILTER_SLOTS = 0;
 
 // Scratch after the sketch's: the 264 features and the 4 network outputs.
 constexpr uint64_t LEARN_SCRATCH = 2048;
@@ -782,6 +793,50 @@ void choose_variant(int variant, int64_t est, int64_t n_rows, int words, bool p_
       choose_layers(est, words, plan);
       if (plan->variant == REL_VAR_GLOBAL && p_ok) choose_partitioned(est, n_rows, plan);
   }
+}
+
+// The exact distinct count of one int32 / int64 key column (no filter) in
+// workspace ws of HEADER_BYTES + 8 * set_slots bytes.  First one pass with a
+// key set of at most EXACT_SET_FIRST_BYTES (load <= ~0.5 up to 1.6e7 distinct
+// keys; its random reads mostly hit L2); when the distinct keys overflow it,
+// the whole workspace is split into K sets of at most EXACT_SET_FIRST_BYTES
+// each (K <= 16) and K passes each count the keys of one hash range.  Every
+// attempt gives the same count.
+rel_status exact_distinct(const void* keys, int32_t key_type, int64_t n_rows, void* ws,
+                          uint64_t set_slots, int64_t* est, cudaStream_t st) {
+  DistinctParams dp;
+  std::memset(&dp, 0, sizeof dp);
+  dp.keys = keys;
+  dp.n_rows = n_rows;
+  dp.hdr = (WsHeader*)ws;
+  dp.filter_slots = EXACT_FILTER_SLOTS;
+  const uint64_t total_buckets = set_slots / DS_BUCKET_SLOTS;  // set_slots >= 16
+  const uint64_t first_buckets = EXACT_SET_FIRST_BYTES / (8ull * DS_BUCKET_SLOTS);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    uint32_t passes = 1;
+    uint64_t buckets = total_buckets < first_buckets ? total_buckets : first_buckets;
+    if (attempt == 1) {
+      if (total_buckets <= first_buckets) break;  // the first set was already the full one
+      passes = (uint32_t)std::min<uint64_t>(16, (total_buckets + first_buckets - 1) / first_buckets);
+      buckets = total_buckets / passes;
+    }
+    cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + 8ull * DS_BUCKET_SLOTS * buckets * passes, st);
+    if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+    rel_status r;
+    for (uint32_t k = 0; k < passes; ++k) {
+      dp.n_pass = passes;
+      dp.pass = k;
+      dp.n_buckets = buckets;
+      dp.set = (uint64_t*)((uint8_t*)ws + HEADER_BYTES) + (uint64_t)k * buckets * DS_BUCKET_SLOTS;
+      if ((r = distinct_launch(dp, key_type, st))) return r;
+    }
+    HostHeader h;
+    if ((r = read_header(ws, &h, st))) return r;
+    if (h.overflow) continue;
+    *est = (int64_t)h.aux + (h.n_side > 0 ? 1 : 0);
+    return REL_OK;
+  }
+  return set_error("plan: key set overflow"), REL_E_OVERFLOW;
 }
 
 rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint, void* ws,
@@ -874,34 +929,33 @@ rel_status plan_groupby(const rel_groupby_desc* d, uint32_t flags, int64_t hint,
       const int32_t kt = kd.cols[keys[0]].type;
       const bool stream_keys = !(flags & REL_PLAN_GENERIC) && kd.n_keys == 1 &&
                                kd.n_preds == 0 && (kt == REL_I64 || kt == REL_I32);
-      // First a key set of at most EXACT_SET_L2_SLOTS slots (128 MB: its
-      // probes stay in L2, and the memset is small); only when the distinct
-      // keys overflow it, the full 2 x rows set.  Both give the same count.
-      uint64_t try_slots = set_slots < EXACT_SET_L2_SLOTS ? set_slots : EXACT_SET_L2_SLOTS;
-      for (;;) {
-        kp.log2_slots = log2_pow2(try_slots);
-        kp.max_probe = (uint32_t)(try_slots < 4096 ? try_slots : 4096);
-        kp.smem_slots = 2048;
-        kp.shared_probes = 4;
-        cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + 8ull * try_slots, st);
-        if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
-        if (stream_keys) {
-          kp.smem_slots = SHARED_MAX_SLOTS;  // 32 KB set per CTA: keeps more of the hot keys
-          r = gb_launch_keyset_stream(kp, kt, st);  // streaming loads, keys only
-        } else {
-          r = run_main(kp, kshape, MODE_KEYSET, st);
-        }
+      if (stream_keys) {
+        r = exact_distinct(kd.cols[keys[0]].data, kt, d->n_rows, ws, set_slots, &est, st);
         if (r) return r;
-        HostHeader h;
-        if ((r = read_header(ws, &h, st))) return r;
-        if (h.timeout) return set_error("plan: a device wait timed out"), REL_E_TIMEOUT;
-        if (h.overflow && try_slots < set_slots) {
-          try_slots = set_slots;
-          continue;
+      } else {
+        // First a key set of at most EXACT_SET_L2_SLOTS slots (128 MB: the
+        // memset is small); only when the distinct keys overflow it, the full
+        // 2 x rows set.  Both give the same count.
+        uint64_t try_slots = set_slots < EXACT_SET_L2_SLOTS ? set_slots : EXACT_SET_L2_SLOTS;
+        for (;;) {
+          kp.log2_slots = log2_pow2(try_slots);
+          kp.max_probe = (uint32_t)(try_slots < 4096 ? try_slots : 4096);
+          kp.smem_slots = 2048;
+          kp.shared_probes = 4;
+          cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + 8ull * try_slots, st);
+          if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
+          if ((r = run_main(kp, kshape, MODE_KEYSET, st))) return r;
+          HostHeader h;
+          if ((r = read_header(ws, &h, st))) return r;
+          if (h.timeout) return set_error("plan: a device wait timed out"), REL_E_TIMEOUT;
+          if (h.overflow && try_slots < set_slots) {
+            try_slots = set_slots;
+            continue;
+          }
+          if (h.overflow) return set_error("plan: key set overflow"), REL_E_OVERFLOW;
+          est = (int64_t)h.aux + (h.n_side > 0 ? 1 : 0);
+          break;
         }
-        if (h.overflow) return set_error("plan: key set overflow"), REL_E_OVERFLOW;
-        est = (int64_t)h.aux + (h.n_side > 0 ? 1 : 0);
-        break;
       }
     }
   } else {
@@ -937,7 +991,7 @@ struct JoinLayout {
 JoinLayout join_layout(int64_t n_build) {
   JoinLayout L;
   L.slots = next_pow2((uint64_t)(2 * n_build < 16 ? 16 : 2 * n_build));
-  L.bytes = HEADER_BYTES + L.slots * (8 + sizeof(JoinVal)) +
+  L.bytes = HEADER_BYTES + L.slots * sizeof(JoinSlot) +
             (uint64_t)(n_build > 0 ? n_build : 1) * sizeof(JoinVal);
   return L;
 }
@@ -947,9 +1001,8 @@ JoinParams join_params(const rel_join_table* t) {
   uint8_t* ws = (uint8_t*)t->ws;
   const uint64_t slots = (uint64_t)t->slots;
   p.hdr = (WsHeader*)ws;
-  p.tkeys = (uint64_t*)(ws + HEADER_BYTES);
-  p.tvals = (JoinVal*)(ws + HEADER_BYTES + 8 * slots);
-  p.side = (JoinVal*)(ws + HEADER_BYTES + (8 + sizeof(JoinVal)) * slots);
+  p.slots = (JoinSlot*)(ws + HEADER_BYTES);
+  p.side = (JoinVal*)(ws + HEADER_BYTES + sizeof(JoinSlot) * slots);
   p.log2_slots = t->log2_slots;
   return p;
 }
@@ -1348,6 +1401,11 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   p.log2_slots = log2_pow2((uint64_t)plan->slots);
   p.max_probe = (uint32_t)(plan->slots < 4096 ? plan->slots : 4096);
   if ((r = set_layers(p, plan, m.shape))) return r;
+  p.wait_ns = WAIT_LIMIT_NS;
+  if (plan->flags & REL_PLAN_TEST_STALL) {
+    p.test_stall = 1;
+    p.wait_ns = TEST_WAIT_LIMIT_NS;
+  }
   if (plan->tile_rows || plan->n_stages) {
     const int32_t t = plan->tile_rows, ns = plan->n_stages;
     if (t < 256 || t > 4096 || !is_pow2((uint64_t)t) || ns < 2 || ns > GB_MAX_STAGES)
@@ -1403,7 +1461,7 @@ rel_status rel_join_build(const int64_t* keys, const int64_t* payload, int64_t n
   table->log2_slots = log2_pow2(L.slots);
   table->magic = TABLE_MAGIC;
   cudaStream_t st = as_stream(stream);
-  cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + 8 * L.slots, st);
+  cudaError_t e = cudaMemsetAsync(ws, 0, HEADER_BYTES + sizeof(JoinSlot) * L.slots, st);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaMemsetAsync");
   return join_launch_build(join_params(table), keys, payload, n_build, st);
 }

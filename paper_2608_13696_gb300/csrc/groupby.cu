@@ -761,8 +761,7 @@ __global__ void __launch_bounds__(GB_THREADS) gb_main(const __grid_constant__ Gb
     int64_t k = 0;
     for (; k < mine; ++k) {
       const int s = (int)(k % NS);
-      if (k >= NS &&
-          !mbar_wait_bounded(&empty[s], (uint32_t)((k / NS - 1) & 1), WAIT_LIMIT_NS)) {
+      if (k >= NS && !mbar_wait_bounded(&empty[s], (uint32_t)((k / NS - 1) & 1), p.wait_ns)) {
         atomicOr(&p.hdr->timeout, 1u);
         break;
       }
@@ -777,7 +776,7 @@ __global__ void __launch_bounds__(GB_THREADS) gb_main(const __grid_constant__ Gb
     }
     // the CTA's shared memory must outlive every copy issued into it
     for (int64_t j = (k > NS ? k - NS : 0); j < k; ++j)
-      mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), WAIT_LIMIT_NS);
+      mbar_wait_bounded(&full[j % NS], (uint32_t)((j / NS) & 1), p.wait_ns);
     return;
   }
 
@@ -787,7 +786,7 @@ __global__ void __launch_bounds__(GB_THREADS) gb_main(const __grid_constant__ Gb
   if (USE_TMA) {
     for (int64_t k = 0; k < mine; ++k) {
       const int s = (int)(k % NS);
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / NS) & 1), WAIT_LIMIT_NS)) {
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / NS) & 1), p.wait_ns)) {
         atomicOr(&p.hdr->timeout, 1u);
         *(volatile int*)abort_flag = 1;
         break;
@@ -798,7 +797,9 @@ __global__ void __launch_bounds__(GB_THREADS) gb_main(const __grid_constant__ Gb
         live = live && __shfl_sync(0xffffffffu, f, 0) == 0;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
+      // (test hook: a ring whose stages never come back, so that the
+      // producer's and then the consumers' bounded waits run out)
+      if (lane == 0 && !p.test_stall) mbar_arrive(&empty[s]);
     }
     const int64_t tail0 = n_tiles * T;
     if (live && tail0 < p.n_rows && blockIdx.x == (unsigned)(n_tiles % gridDim.x))
@@ -947,6 +948,8 @@ __device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, uns
   gtab_update<S>(p, ek, x);
 }
 
+constexpr int PA_R = 4;  // record groups in flight per warp in the aggregation pass
+
 // Pass 3: each CTA aggregates whole partitions in a shared-memory table of
 // p.smem_slots slots and writes their groups straight to the output (warp
 // ballot / popc, one atomic per warp).  Every key lives in one partition, so
@@ -988,16 +991,28 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
       // warp's first key (under skew, usually the partition's heavy key) are
       // combined in registers first (0 is every word's identity) and applied
       // once, the other rows go to the table one by one
+      // PA_R groups of 32 records per warp are loaded before any is used
+      // (the pass is bound by load latency)
       const int warp = threadIdx.x >> 5;
-      for (unsigned long long b0 = beg + (unsigned long long)warp * 32; b0 < end; b0 += GB_BLOCK) {
+      for (unsigned long long b00 = beg + (unsigned long long)warp * 32 * PA_R; b00 < end;
+           b00 += (unsigned long long)GB_BLOCK * PA_R) {
+       longlong2 rec[PA_R];
+#pragma unroll
+       for (int rr = 0; rr < PA_R; ++rr) {
+         const unsigned long long i = b00 + (unsigned long long)rr * 32 + lane;
+         rec[rr] = i < end ? __ldcs((const longlong2*)(p.recs + i)) : make_longlong2(0, 0);
+       }
+#pragma unroll
+       for (int rr = 0; rr < PA_R; ++rr) {
+        const unsigned long long b0 = b00 + (unsigned long long)rr * 32;
+        if (b0 >= end) break;  // uniform across the warp
         const unsigned long long i = b0 + lane;
         const bool valid = i < end;
         Vals<A> x;
         uint64_t ek = 0;
         if (valid) {
-          const PartRec r = p.recs[i];
-          ek = r.ek;
-          S::from_val((uint64_t)r.val, x);
+          ek = (uint64_t)rec[rr].x;
+          S::from_val((uint64_t)rec[rr].y, x);
         } else {
 #pragma unroll
           for (int a = 0; a < A; ++a) x.v[a] = 0;
@@ -1029,6 +1044,7 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
         // brings the combined words, the other keys' lanes their own row,
         // the first key's other lanes nothing
         if (valid && (!combine || !mine || lane == ld)) part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
+       }
       }
     }
     __syncthreads();

@@ -97,6 +97,8 @@ struct GbParams {
   int32_t log2_slots;
   uint32_t max_probe;
   WsHeader* hdr;
+  uint64_t wait_ns;     // limit of every bounded device wait (WAIT_LIMIT_NS)
+  uint32_t test_stall;  // test hook: consumers never hand a stage back
 };
 
 struct GbOut {
@@ -120,8 +122,6 @@ rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st);
 // key/value shapes, streaming; grid = p.fixed_grid CTAs in both passes.
 bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot);
 rel_status gb_launch_ppass_stream(const GbParams& p, int shape, bool scatter, cudaStream_t st);
-// Exact distinct count of one int32 / int64 key column without a filter.
-rel_status gb_launch_keyset_stream(const GbParams& p, int key_type, cudaStream_t st);
 // Aggregate-array width the kernel for a shape is compiled with.
 int gb_shape_width(int shape);
 // Shared-memory bytes of the per-CTA tables (before the staging ring).

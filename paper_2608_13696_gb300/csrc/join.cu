@@ -3,11 +3,16 @@
 // The paper's join runs three kernels over a hash table that is read
 // randomly: insert (build), count (size the output) and retrieve (emit the
 // matches), with the payload brought in by a separate gather (Sec. 7,
-// Table 9).  Here the table is an open-addressing array at load <= 1/2 --
-// 2^21 slots x 24 bytes for a 10^6-row build side, so it stays resident in
-// the 129 MB L2 while the probe side streams from HBM -- and the probe writes
-// (probe_idx, build_idx, payload) directly: each warp compacts its lanes'
-// matches with a ballot / popc and reserves output space with one atomic.
+// Table 9), and finds count and retrieve bound by instruction issue and
+// memory latency on GH200.  Here the table is an open-addressing array at
+// load <= 1/2 whose 32-byte slots hold the key, the payload and the build row
+// index together -- 2^21 slots (64 MB) for a 10^6-row build side, which stays
+// in the GB300's L2 while the probe keys stream from HBM -- so a probe reads
+// key and payload with one 256-bit load (the gather is fused into the probe:
+// one L2 request per probed slot).  Every probe row's first slot is loaded
+// before any is resolved, probe keys arrive in 16-byte vector loads, and each
+// warp compacts its lanes' matches with a ballot / popc and reserves output
+// space with one atomic.
 #include "join.cuh"
 
 namespace rel {
@@ -15,6 +20,23 @@ namespace rel {
 namespace {
 
 constexpr int J_BLOCK = 256;
+
+// One slot, marked evict-last in L2 so that the table outlives the streamed
+// probe keys (evict-first) and the streamed outputs.
+__device__ __forceinline__ void ld_slot(const JoinSlot* p, uint64_t& ek, int64_t& payload,
+                                        int32_t& bidx) {
+  unsigned long long a, b, c, d;
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+      "ld.global.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], pol;\n\t}"
+      : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+      : "l"(p));
+  (void)d;
+  ek = a;
+  payload = (int64_t)b;
+  bidx = (int32_t)(uint32_t)c;
+}
 
 __global__ void __launch_bounds__(J_BLOCK) join_build_k(const __grid_constant__ JoinParams p,
                                                         const int64_t* __restrict__ keys,
@@ -25,20 +47,21 @@ __global__ void __launch_bounds__(J_BLOCK) join_build_k(const __grid_constant__ 
   for (int64_t j = (int64_t)blockIdx.x * J_BLOCK + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * J_BLOCK) {
     const uint64_t ek = (uint64_t)__ldg((const long long*)keys + j) ^ KEY_FLIP;
-    const JoinVal v{__ldg((const long long*)payload + j), (int32_t)j, 0};
+    const long long pay = __ldg((const long long*)payload + j);
     if (ek == 0) {  // INT64_MIN: side list
       const unsigned long long pos = atomicAdd(&p.hdr->n_side, 1ull);
-      p.side[pos] = v;
+      p.side[pos] = JoinVal{pay, (int32_t)j, 0};
       continue;
     }
     uint64_t s = slot_of(ek, p.log2_slots);
     bool placed = false;
     for (uint64_t i = 0; i <= mask; ++i) {
-      uint64_t cur = ld_relaxed(p.tkeys + s);
+      uint64_t cur = ld_relaxed((const uint64_t*)&p.slots[s].ek);
       if (cur == 0) {
-        cur = atomicCAS((unsigned long long*)(p.tkeys + s), 0ull, (unsigned long long)ek);
+        cur = atomicCAS(&p.slots[s].ek, 0ull, (unsigned long long)ek);
         if (cur == 0) {
-          p.tvals[s] = v;
+          p.slots[s].payload = pay;
+          p.slots[s].bidx = (int32_t)j;
           placed = true;
           break;
         }
@@ -57,35 +80,38 @@ __global__ void __launch_bounds__(J_BLOCK) join_build_k(const __grid_constant__ 
 // Next match of a lane's probe sequence.  State: slot s (table) or index s
 // into the side list (key INT64_MIN).  Returns false when the sequence ends.
 __device__ __forceinline__ bool next_match(const JoinParams& p, uint64_t ek, bool side,
-                                           uint64_t n_side, uint64_t& s, JoinVal& out) {
+                                           uint64_t n_side, uint64_t& s, int64_t& pay,
+                                           int32_t& bidx) {
   if (side) {
     if (s >= n_side) return false;
-    out = p.side[s++];
+    const JoinVal v = p.side[s++];
+    pay = v.payload;
+    bidx = v.bidx;
     return true;
   }
   const uint64_t mask = (1ull << p.log2_slots) - 1;
   for (uint64_t i = 0; i <= mask; ++i) {
-    const uint64_t k = p.tkeys[s];
+    uint64_t k;
+    ld_slot(p.slots + s, k, pay, bidx);
     if (k == 0) return false;
-    const uint64_t cur = s;
     s = (s + 1) & mask;
-    if (k == ek) {
-      out = p.tvals[cur];
-      return true;
-    }
+    if (k == ek) return true;
   }
   return false;
 }
 
-// Probe with J_IT rows per thread in flight.  Every row's first slot and, for
-// a hit, its payload are loaded for all J_IT rows before any is used, so a
-// warp keeps J_IT independent L2 round trips outstanding instead of one.
-// With unique build keys (no duplicate seen while building) a row stops at
-// its first match; otherwise -- and for the INT64_MIN side list -- it walks
-// its whole probe sequence.  Matches are written in row-slot order: one
-// atomic per warp reserves the tile's output, each row-slot's matches are
-// compacted with a ballot, so consecutive lanes write consecutive entries.
-constexpr int J_IT = 4;
+// Probe with J_IT rows per thread in flight, in groups of J_G: every row of
+// a group has its first slot (key, payload, build index) loaded before any is
+// resolved, so a warp keeps J_G independent L2 round trips outstanding per
+// lane.  With unique build keys (no duplicate seen while building) a row
+// stops at its first match; otherwise -- and for the INT64_MIN side list --
+// it walks its whole probe sequence.  Matches are written in row-slot order:
+// one atomic per warp and group reserves the output, each row-slot's matches
+// are compacted with a ballot, so consecutive lanes write consecutive
+// entries.  Rows: base + v * 2 * J_BLOCK + 2 * tid + {0, 1}, probe keys read
+// two at a time with 16-byte loads.
+constexpr int J_IT = 8;
+constexpr int J_G = 4;
 
 template <bool EMIT>
 __global__ void __launch_bounds__(J_BLOCK) join_probe_fast_k(const __grid_constant__ JoinParams p,
@@ -97,96 +123,109 @@ __global__ void __launch_bounds__(J_BLOCK) join_probe_fast_k(const __grid_consta
   const uint64_t mask = (1ull << p.log2_slots) - 1;
   const bool unique = ld_relaxed_u32(&p.hdr->dups) == 0;
   const uint64_t n_side = p.hdr->n_side;
+  const bool vec = (uintptr_t)probe % 16 == 0;
   unsigned long long counted = 0;
   const int64_t tile = (int64_t)J_BLOCK * J_IT;
   for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
-    uint64_t ek[J_IT], s[J_IT], k[J_IT];
-    bool hit[J_IT], slow[J_IT];
+    uint64_t ek[J_IT];
+    int64_t row[J_IT];
 #pragma unroll
-    for (int j = 0; j < J_IT; ++j) {
-      const int64_t i = base + (int64_t)j * J_BLOCK + threadIdx.x;
-      ek[j] = i < n ? ((uint64_t)__ldcs((const long long*)probe + i) ^ KEY_FLIP) : 0;
-      s[j] = slot_of(ek[j], p.log2_slots);
-    }
-#pragma unroll
-    for (int j = 0; j < J_IT; ++j) k[j] = p.tkeys[s[j]];
-#pragma unroll
-    for (int j = 0; j < J_IT; ++j) {
-      const int64_t i = base + (int64_t)j * J_BLOCK + threadIdx.x;
-      const bool valid = i < n;
-      slow[j] = valid && (ek[j] == 0 || !unique);
-      hit[j] = false;
-      if (valid && !slow[j]) {
-        for (uint64_t step = 0; step <= mask && k[j] != 0 && k[j] != ek[j]; ++step) {
-          s[j] = (s[j] + 1) & mask;
-          k[j] = p.tkeys[s[j]];
-        }
-        hit[j] = k[j] == ek[j];
+    for (int v = 0; v < J_IT / 2; ++v) {
+      const int64_t r = base + (int64_t)v * 2 * J_BLOCK + 2 * threadIdx.x;
+      row[2 * v] = r;
+      row[2 * v + 1] = r + 1;
+      if (vec && r + 1 < n) {
+        const longlong2 kk = __ldcs((const longlong2*)(probe + r));
+        ek[2 * v] = (uint64_t)kk.x ^ KEY_FLIP;
+        ek[2 * v + 1] = (uint64_t)kk.y ^ KEY_FLIP;
+      } else {
+        ek[2 * v] = r < n ? (uint64_t)__ldcs((const long long*)probe + r) ^ KEY_FLIP : 0;
+        ek[2 * v + 1] = r + 1 < n ? (uint64_t)__ldcs((const long long*)probe + r + 1) ^ KEY_FLIP : 0;
       }
     }
-    JoinVal v[J_IT];
-    if (EMIT) {
 #pragma unroll
-      for (int j = 0; j < J_IT; ++j)
-        if (hit[j]) v[j] = p.tvals[s[j]];
-    }
-    unsigned m[J_IT];
-    unsigned total = 0;
+    for (int g = 0; g < J_IT; g += J_G) {
+      uint64_t s[J_G], k[J_G];
+      int64_t pay[J_G];
+      int32_t bidx[J_G];
+      bool hit[J_G], slow[J_G];
 #pragma unroll
-    for (int j = 0; j < J_IT; ++j) {
-      m[j] = __ballot_sync(0xffffffffu, hit[j]);
-      total += __popc(m[j]);
-    }
-    if (!EMIT) {
-      counted += lane == 0 ? total : 0;
-    } else if (total) {
-      unsigned long long wb = 0;
-      if (lane == 0) wb = atomicAdd(&p.hdr->n_out, (unsigned long long)total);
-      wb = __shfl_sync(0xffffffffu, wb, 0);
+      for (int q = 0; q < J_G; ++q) {
+        const bool valid = row[g + q] < n;
+        slow[q] = valid && (ek[g + q] == 0 || !unique);
+        s[q] = slot_of(ek[g + q], p.log2_slots);
+        k[q] = 0;
+        if (valid && !slow[q]) ld_slot(p.slots + s[q], k[q], pay[q], bidx[q]);
+      }
 #pragma unroll
-      for (int j = 0; j < J_IT; ++j) {
-        if (hit[j]) {
-          const uint64_t pos = wb + __popc(m[j] & lt);
-          if (pos < (uint64_t)o.capacity) {
-            o.probe_idx[pos] = (int32_t)(base + (int64_t)j * J_BLOCK + threadIdx.x);
-            o.build_idx[pos] = v[j].bidx;
-            o.payload[pos] = v[j].payload;
+      for (int q = 0; q < J_G; ++q) {
+        hit[q] = false;
+        if (row[g + q] < n && !slow[q]) {
+          for (uint64_t step = 0; step <= mask && k[q] != 0 && k[q] != ek[g + q]; ++step) {
+            s[q] = (s[q] + 1) & mask;
+            ld_slot(p.slots + s[q], k[q], pay[q], bidx[q]);
           }
+          hit[q] = k[q] == ek[g + q];
         }
-        wb += __popc(m[j]);
       }
-    }
-    // rows that may match more than once (or the INT64_MIN side list): walk
-    // the whole sequence, one match per round, compacted per round
+      unsigned m[J_G];
+      unsigned total = 0;
 #pragma unroll
-    for (int j = 0; j < J_IT; ++j) {
-      if (!__any_sync(0xffffffffu, slow[j])) continue;
-      const int64_t i = base + (int64_t)j * J_BLOCK + threadIdx.x;
-      const bool side = ek[j] == 0;
-      uint64_t q = side ? 0 : slot_of(ek[j], p.log2_slots);
-      bool active = slow[j];
-      while (__any_sync(0xffffffffu, active)) {
-        JoinVal w;
-        bool h = false;
-        if (active) {
-          h = next_match(p, ek[j], side, n_side, q, w);
-          active = h;
-        }
-        if (!EMIT) {
-          counted += h;
-          continue;
-        }
-        const unsigned mm = __ballot_sync(0xffffffffu, h);
-        if (!mm) continue;
+      for (int q = 0; q < J_G; ++q) {
+        m[q] = __ballot_sync(0xffffffffu, hit[q]);
+        total += __popc(m[q]);
+      }
+      if (!EMIT) {
+        counted += lane == 0 ? total : 0;
+      } else if (total) {
         unsigned long long wb = 0;
-        if (lane == 0) wb = atomicAdd(&p.hdr->n_out, (unsigned long long)__popc(mm));
+        if (lane == 0) wb = atomicAdd(&p.hdr->n_out, (unsigned long long)total);
         wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (h) {
-          const uint64_t pos = wb + __popc(mm & lt);
-          if (pos < (uint64_t)o.capacity) {
-            o.probe_idx[pos] = (int32_t)i;
-            o.build_idx[pos] = w.bidx;
-            o.payload[pos] = w.payload;
+#pragma unroll
+        for (int q = 0; q < J_G; ++q) {
+          if (hit[q]) {
+            const uint64_t pos = wb + __popc(m[q] & lt);
+            if (pos < (uint64_t)o.capacity) {  // streaming stores: keep the table in L2
+              __stcs(o.probe_idx + pos, (int32_t)row[g + q]);
+              __stcs(o.build_idx + pos, bidx[q]);
+              __stcs((long long*)o.payload + pos, (long long)pay[q]);
+            }
+          }
+          wb += __popc(m[q]);
+        }
+      }
+      // rows that may match more than once (or the INT64_MIN side list): walk
+      // the whole sequence, one match per round, compacted per round
+#pragma unroll
+      for (int q = 0; q < J_G; ++q) {
+        if (!__any_sync(0xffffffffu, slow[q])) continue;
+        const bool side = ek[g + q] == 0;
+        uint64_t qs = side ? 0 : slot_of(ek[g + q], p.log2_slots);
+        bool active = slow[q];
+        while (__any_sync(0xffffffffu, active)) {
+          int64_t wp = 0;
+          int32_t wi = 0;
+          bool h = false;
+          if (active) {
+            h = next_match(p, ek[g + q], side, n_side, qs, wp, wi);
+            active = h;
+          }
+          if (!EMIT) {
+            counted += h;
+            continue;
+          }
+          const unsigned mm = __ballot_sync(0xffffffffu, h);
+          if (!mm) continue;
+          unsigned long long wb = 0;
+          if (lane == 0) wb = atomicAdd(&p.hdr->n_out, (unsigned long long)__popc(mm));
+          wb = __shfl_sync(0xffffffffu, wb, 0);
+          if (h) {
+            const uint64_t pos = wb + __popc(mm & lt);
+            if (pos < (uint64_t)o.capacity) {
+              o.probe_idx[pos] = (int32_t)row[g + q];
+              o.build_idx[pos] = wi;
+              o.payload[pos] = wp;
+            }
           }
         }
       }

@@ -13,11 +13,21 @@ struct alignas(16) JoinVal {
   int32_t pad;
 };
 
-// Workspace layout: [WsHeader 256 B][tkeys slots x 8 B][tvals slots x 16 B]
-//                   [side n_build x 16 B]
+// One slot of the single-call join table: the stored key (key ^ KEY_FLIP,
+// 0 = empty), the build row's payload and index -- one 32-byte sector, so a
+// probe reads key and payload with one 256-bit load.
+struct alignas(32) JoinSlot {
+  unsigned long long ek;
+  long long payload;
+  int32_t bidx;
+  int32_t pad;
+  long long pad2;
+};
+static_assert(sizeof(JoinSlot) == 32, "one sector per slot");
+
+// Workspace layout: [WsHeader 256 B][slots x 32 B][side n_build x 16 B]
 struct JoinParams {
-  uint64_t* tkeys;   // stored keys (key ^ KEY_FLIP), 0 = empty
-  JoinVal* tvals;
+  JoinSlot* slots;
   JoinVal* side;     // build rows whose key is INT64_MIN
   WsHeader* hdr;
   int32_t log2_slots;

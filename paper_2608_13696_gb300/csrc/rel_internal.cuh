@@ -138,6 +138,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// L2 policy for data that should stay resident (a hash table probed while a
+// column streams past with evict-first loads).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -188,6 +196,8 @@ static_assert(sizeof(WsHeader) <= 256, "header fits in 256 bytes");
 constexpr uint64_t HEADER_BYTES = 256;
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s for any single wait
+// the same limit under the test hook REL_PLAN_TEST_STALL
+constexpr uint64_t TEST_WAIT_LIMIT_NS = 20000000ull;  // 20 ms
 
 }  // namespace rel
 

@@ -33,7 +33,6 @@ constexpr int pin_max() {
 }
 constexpr int ST_PIN_LIMIT = 16;
 constexpr uint32_t ST_SMEM_MULT = 0x85EBCA77u;
-constexpr int ST_KS_BLOCK = 256;
 
 template <int NA>
 __device__ __forceinline__ void words_of(uint64_t v, uint64_t (&w)[NA]) {
@@ -287,131 +286,6 @@ __global__ void __launch_bounds__(ST_BLOCK, 6) gb_stream_k(const __grid_constant
   }
 }
 
-// The exact distinct count (the plain form's pre-pass) for one int32 / int64
-// key column and no filter: the same streaming loads, keys only; a CTA-shared
-// set drops the keys this CTA has already sent, every first sight goes to the
-// global key set, whose claims are the count.  Once the set has overflowed
-// the count is void (the caller retries with a larger set), so a thread that
-// sees the overflow stops reading.
-template <class KT>
-__global__ void __launch_bounds__(ST_KS_BLOCK, 4) gb_keyset_stream_k(const __grid_constant__ GbParams p) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  uint64_t* sk = (uint64_t*)sm;
-  const int tid = threadIdx.x;
-  const uint32_t S = p.smem_slots, smask = S - 1;
-  for (uint32_t i = tid; i < S; i += ST_KS_BLOCK) sk[i] = 0;
-  __syncthreads();
-  const KT* keys = (const KT*)p.col[p.key_col[0]];
-  const int64_t n = p.n_rows;
-  constexpr int64_t CHUNK = (int64_t)ST_KS_BLOCK * ST_U;
-  const bool vec = (uintptr_t)keys % (2 * sizeof(KT)) == 0;
-  const uint64_t mask = (1ull << p.log2_slots) - 1;
-  unsigned long long claims = 0, side = 0;
-  bool stop = false;  // the set overflowed: the count is void, so stop reading
-  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n && !stop;
-       base += (int64_t)gridDim.x * CHUNK) {
-    uint64_t ek[ST_U];
-    bool ok[ST_U];
-    if (vec && base + CHUNK <= n) {
-#pragma unroll
-      for (int j = 0; j < ST_U / 2; ++j) {
-        const int64_t r = base + (int64_t)j * 2 * ST_KS_BLOCK + 2 * tid;
-        int64_t k0, k1;
-        KeyPair<KT>::split(__ldcs((const typename KeyPair<KT>::V*)(keys + r)), k0, k1);
-        ek[2 * j] = (uint64_t)k0 ^ KEY_FLIP;
-        ek[2 * j + 1] = (uint64_t)k1 ^ KEY_FLIP;
-        ok[2 * j] = ok[2 * j + 1] = true;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < ST_U; ++j) {
-        const int64_t r = base + (int64_t)(j / 2) * 2 * ST_KS_BLOCK + 2 * tid + (j & 1);
-        ok[j] = r < n;
-        ek[j] = ok[j] ? ((uint64_t)(int64_t)keys[r] ^ KEY_FLIP) : 0;
-      }
-    }
-    bool need[ST_U];
-#pragma unroll
-    for (int j = 0; j < ST_U; ++j) {
-      need[j] = false;
-      if (!ok[j]) continue;
-      if (ek[j] == 0) {
-        ++side;
-        continue;
-      }
-      uint32_t s = small_slot_of(ek[j], smask, ST_SMEM_MULT);
-      bool seen = false, first = false;
-      for (uint32_t i = 0; i < p.shared_probes; ++i) {
-        uint64_t k = *(volatile uint64_t*)(sk + s);
-        if (k == 0) {
-          k = atomicCAS((unsigned long long*)(sk + s), 0ull, (unsigned long long)ek[j]);
-          if (k == 0) {
-            first = true;
-            break;
-          }
-        }
-        if (k == ek[j]) {
-          seen = true;
-          break;
-        }
-        s = (s + 1) & smask;
-      }
-      need[j] = first || !seen;
-    }
-    uint64_t gs[ST_U], gk[ST_U];
-#pragma unroll
-    for (int j = 0; j < ST_U; ++j) {
-      if (!need[j]) continue;
-      gs[j] = slot_of(ek[j], p.log2_slots);
-      gk[j] = __ldcg((const unsigned long long*)(p.tkeys + gs[j]));
-    }
-#pragma unroll
-    for (int j = 0; j < ST_U; ++j) {
-      if (!need[j]) continue;
-      uint64_t s = gs[j], k = gk[j];
-      bool done = false;
-      for (uint32_t i = 0; i < p.max_probe; ++i) {
-        if (k == ek[j]) {
-          done = true;
-          break;
-        }
-        if (k == 0) {
-          k = atomicCAS((unsigned long long*)(p.tkeys + s), 0ull, (unsigned long long)ek[j]);
-          if (k == 0) {
-            ++claims;
-            done = true;
-            break;
-          }
-          if (k == ek[j]) {
-            done = true;
-            break;
-          }
-        }
-        s = (s + 1) & mask;
-        if ((i & 31) == 31 && ld_relaxed_u32(&p.hdr->overflow)) {
-          done = stop = true;  // already overflowed: the count is discarded
-          break;
-        }
-        k = __ldcg((const unsigned long long*)(p.tkeys + s));
-      }
-      if (!done) {
-        atomicOr(&p.hdr->overflow, 1u);
-        stop = true;
-      }
-    }
-  }
-  // one atomic per warp for the counts
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    claims += __shfl_xor_sync(0xffffffffu, claims, o);
-    side += __shfl_xor_sync(0xffffffffu, side, o);
-  }
-  if ((tid & 31) == 0) {
-    if (claims) atomicAdd(&p.hdr->aux, claims);
-    if (side) atomicAdd(&p.hdr->n_side, side);
-  }
-}
-
 // Partitioned variant, passes 1 and 2, streaming: a CTA counts its rows per
 // partition (pass 1), then -- after the scan turned the counts into
 // positions -- writes each row as a (key, value) record at its partition's
@@ -460,10 +334,9 @@ __global__ void __launch_bounds__(SP_BLOCK) gb_ppass_stream_k(const __grid_const
   const int64_t n = p.n_rows;
   constexpr int64_t CHUNK = (int64_t)SP_BLOCK * ST_U;
   const bool vec = ((uintptr_t)keys % (2 * sizeof(KT)) == 0) && ((uintptr_t)vals % 16 == 0);
-  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n; base += (int64_t)gridDim.x * CHUNK) {
-    uint64_t ek[ST_U];
-    uint64_t val[ST_U];
-    bool ok[ST_U];
+  // rows base + j * 2 * SP_BLOCK + 2 * tid + {0, 1}; the next chunk's loads
+  // go out before this chunk is worked on (the pass is bound by load latency)
+  auto load = [&](int64_t base, uint64_t(&ek)[ST_U], uint64_t(&val)[ST_U], uint32_t& ok) {
     if (vec && base + CHUNK <= n) {
 #pragma unroll
       for (int j = 0; j < ST_U / 2; ++j) {
@@ -477,20 +350,31 @@ __global__ void __launch_bounds__(SP_BLOCK) gb_ppass_stream_k(const __grid_const
           val[2 * j] = (uint64_t)vv.x;
           val[2 * j + 1] = (uint64_t)vv.y;
         }
-        ok[2 * j] = ok[2 * j + 1] = true;
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < ST_U; ++j) {
-        const int64_t r = base + (int64_t)(j / 2) * 2 * SP_BLOCK + 2 * tid + (j & 1);
-        ok[j] = r < n;
-        ek[j] = ok[j] ? ((uint64_t)(int64_t)keys[r] ^ KEY_FLIP) : 0;
-        if (SCATTER) val[j] = ok[j] ? (uint64_t)vals[r] : 0;
-      }
+      ok = (1u << ST_U) - 1;
+      return;
     }
+    ok = 0;
 #pragma unroll
     for (int j = 0; j < ST_U; ++j) {
-      if (!ok[j]) continue;
+      const int64_t r = base + (int64_t)(j / 2) * 2 * SP_BLOCK + 2 * tid + (j & 1);
+      const bool in = r < n;
+      ek[j] = in ? ((uint64_t)(int64_t)keys[r] ^ KEY_FLIP) : 0;
+      if (SCATTER) val[j] = in ? (uint64_t)vals[r] : 0;
+      ok |= (in ? 1u : 0u) << j;
+    }
+  };
+  const int64_t step = (int64_t)gridDim.x * CHUNK;
+  uint64_t ek[ST_U], val[ST_U];
+  uint32_t okm = 0;
+  if ((int64_t)blockIdx.x * CHUNK < n) load((int64_t)blockIdx.x * CHUNK, ek, val, okm);
+  for (int64_t base = (int64_t)blockIdx.x * CHUNK; base < n; base += step) {
+    uint64_t nek[ST_U], nval[ST_U];
+    uint32_t nok = 0;
+    if (base + step < n) load(base + step, nek, nval, nok);
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      if (!(okm >> j & 1)) continue;
       if (PIN) {
         const uint32_t s = small_slot_of(ek[j], tmask, p.tiny_mult);
         if (pk[s] == ek[j] && ek[j] != 0) {
@@ -531,6 +415,12 @@ __global__ void __launch_bounds__(SP_BLOCK) gb_ppass_stream_k(const __grid_const
         p.recs[pos] = r;
       }
     }
+#pragma unroll
+    for (int j = 0; j < ST_U; ++j) {
+      ek[j] = nek[j];
+      if (SCATTER) val[j] = nval[j];
+    }
+    okm = nok;
   }
   __syncthreads();
   if (!SCATTER) {
@@ -647,37 +537,6 @@ bool gb_stream_eligible(const GbParams& p, int shape, int n_hot) {
   // a large shared table would leave too few resident threads for the
   // global probes' latency: that case stays with the fused kernel
   return stream_smem(na, pin, p.smem_slots != 0, p.smem_slots) <= 80 * 1024;
-}
-
-template <class KT>
-rel_status launch_keyset(const GbParams& p, cudaStream_t st) {
-  auto kern = gb_keyset_stream_k<KT>;
-  const size_t smem = 8ull * p.smem_slots;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(keyset)");
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ST_KS_BLOCK, smem);
-  if (e != cudaSuccess) return relhost::cuda_fail(e, "occupancy(keyset)");
-  if (occ < 1) return relhost::set_error("group-by: key-set kernel does not fit"), REL_E_UNSUPPORTED;
-  const int64_t chunks = (p.n_rows + (int64_t)ST_KS_BLOCK * ST_U - 1) / ((int64_t)ST_KS_BLOCK * ST_U);
-  int64_t grid = (int64_t)relhost::device_sms() * occ;
-  if (grid > chunks) grid = chunks;
-  if (grid < 1) grid = 1;
-  relhost::launch_begin(relhost::K_GB_KEYSET, st);
-  kern<<<(int)grid, ST_KS_BLOCK, smem, st>>>(p);
-  relhost::launch_end(relhost::K_GB_KEYSET, st);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(keyset)");
-}
-
-rel_status gb_launch_keyset_stream(const GbParams& p, int key_type, cudaStream_t st) {
-  if (p.n_rows == 0) return REL_OK;
-  if (p.smem_slots < 16 || (p.smem_slots & (p.smem_slots - 1)) || p.smem_slots > SHARED_MAX_SLOTS)
-    return relhost::set_error("group-by: key-set table must be a power of two in [16, 4096]"),
-           REL_E_INVALID;
-  if (key_type == REL_I64) return launch_keyset<int64_t>(p, st);
-  if (key_type == REL_I32) return launch_keyset<int32_t>(p, st);
-  return relhost::set_error("group-by: key-set kernel needs an int32 or int64 key"), REL_E_INVALID;
 }
 
 bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot) {

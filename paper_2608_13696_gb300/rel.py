@@ -31,6 +31,7 @@ OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
 VAR_AUTO, VAR_SMEM, VAR_GLOBAL, VAR_PARTITIONED = 0, 1, 2, 3
 PLAN_EXACT, PLAN_LEARNED, PLAN_GENERIC, PLAN_SKETCH = 1, 2, 4, 8
 PLAN_FELL_BACK = 0x10000
+PLAN_TEST_STALL = 0x40000000  # test hook: the staged kernel's ring never drains
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 264, 64, 4, 21380
 
 

@@ -127,3 +127,25 @@ def test_launch_units():
     assert bench.launch_units("zipf", sz) == 200_000_000
     assert bench.launch_units("join", sz) == 16_000_000
     assert bench.launch_units("lineitem", sz) == 1_000_000
+
+
+def test_binding_roofline_picks_the_higher_utilisation():
+    sz = bench.full_sizes(False)
+    # 1.6 GB in 5 ms on a 6700 GB/s roof: 4.8 % of HBM; 2.35e9 warp instructions
+    # in 5 ms against 152 x 4 x 2.07e9: 37 % of issue -> issue binds
+    roof, instr = bench.binding_roofline("zipf", "gb_main_keyset", 1.6e9, 5.0, 6700.0, "measured",
+                                         5.6e9, 2.35e9, 152, 2070.0, sz)
+    assert roof["bound"] == "alu"
+    assert abs(roof["frac"] - 2.35e9 / 5e-3 / (152 * 4 * 2.07e9)) < 1e-9
+    assert abs(roof["hbm"]["frac"] - 1.6e9 / 5e-3 / 6700e9) < 1e-12
+    assert abs(instr["warp_inst_per_row"] - 2.35e9 / 2e8) < 1e-9
+    assert abs(instr["warp_inst_per_sector"] - 2.35e9 / (5.6e9 / 32)) < 1e-9
+    # a streaming kernel: 3.2 GB in 0.6 ms (80 % of HBM), few instructions -> HBM binds
+    roof, _ = bench.binding_roofline("fourkeys", "gb_stream", 3.2e9, 0.6, 6700.0, "measured",
+                                     3.3e9, 4e8, 152, 2070.0, sz)
+    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert abs(roof["frac"] - 3.2e9 / 0.6e-3 / 6700e9) < 1e-12 and roof["issue_frac"] < roof["frac"]
+    # no capture: HBM only
+    roof, instr = bench.binding_roofline("zipf", "x", 1e9, 1.0, 6700.0, "measured", None, None,
+                                         152, None, sz)
+    assert roof["bound"] == "hbm" and instr is None

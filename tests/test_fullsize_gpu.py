@@ -58,7 +58,7 @@ def test_plain_plan_every_group(big):
     if kind == "zipf":
         assert plan.variant == rel.VAR_PARTITIONED
     else:
-        assert plan.tiny_slots == 8
+        assert plan.n_hot == 4  # every key pinned in thread-private accumulators
     _assert_every_group(canon_groupby(*rel.groupby(q, plan=plan)), ek, ea)
 
 

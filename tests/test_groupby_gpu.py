@@ -171,6 +171,29 @@ def test_overflow_is_reported_not_hung():
     assert k.numel() == len(np.unique(keys))
 
 
+def test_device_wait_gives_up_and_the_stream_stays_usable():
+    """Failure detection without a GPU fault: under the test hook the staged
+    kernel's consumers never hand a stage back, so the producer's bounded
+    wait and then the consumers' run out (20 ms) and the call returns
+    REL_E_TIMEOUT; the next call on the same stream is exact."""
+    import time
+
+    li = synth.lineitem(1_000_000, seed=5)
+    q = oracle.lineitem_query(li)
+    qc = query_to_cuda(q)
+    plan = rel.plan_groupby(qc, groups_hint=8)
+    plan.tile_rows, plan.n_stages = 256, 2  # CTAs get more tiles than stages
+    plan.flags |= rel.PLAN_TEST_STALL
+    t0 = time.perf_counter()
+    with pytest.raises(rel.RelError) as e:
+        rel.groupby(qc, plan=plan)
+    assert e.value.status == rel.REL_E_TIMEOUT
+    assert time.perf_counter() - t0 < 1.5  # the short test limit, not the 2 s one
+    plan.flags &= ~rel.PLAN_TEST_STALL
+    assert_same(q, canon_groupby(*rel.groupby(qc, plan=plan)))
+    assert_same(q, gpu_groupby(q, flags=rel.PLAN_EXACT))
+
+
 # ------------------------------------------ the exact pre-pass's key sets
 
 
@@ -200,3 +223,27 @@ def test_exact_count_within_the_l2_sized_set():
     q = {"cols": [k, v], "keys": [0], "preds": [], "aggs": [("count", 1, [])]}
     plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT)
     assert plan.est_groups == np.unique(k.cpu().numpy()).size
+
+
+@pytest.mark.parametrize("key_type", ["int64", "int32"])
+@pytest.mark.parametrize("offset", [0, 1, 3])
+@pytest.mark.parametrize("n", [1, 7, 2047, 2048 * 9 + 5, 1_000_003])
+def test_exact_count_streaming_shapes(key_type, offset, n):
+    """The streaming distinct count over ragged sizes, unaligned columns
+    (scalar loads) and the INT64_MIN side key: equal to np.unique."""
+    dt = np.int64 if key_type == "int64" else np.int32
+    k = synth.uniform(n + offset, -5 * n, 5 * n, seed=n, tag=5, dtype=dt)
+    if key_type == "int64" and n > 10:
+        k[::11] = np.iinfo(np.int64).min
+        k[1::13] = np.iinfo(np.int64).max
+    v = synth.uniform(n + offset, -9, 9, seed=n, tag=6)
+    kc, vc = cuda(k)[offset:], cuda(v)[offset:]
+    q = {"cols": [kc, vc], "keys": [0], "preds": [], "aggs": [("count", 1, [])]}
+    plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT)
+    assert plan.est_groups == np.unique(k[offset:]).size
+
+
+def test_exact_count_empty_input():
+    kc = torch.empty(0, dtype=torch.int64, device="cuda")
+    q = {"cols": [kc, kc], "keys": [0], "preds": [], "aggs": [("count", 1, [])]}
+    assert rel.plan_groupby(q, flags=rel.PLAN_EXACT).est_groups == 0
