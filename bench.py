@@ -96,6 +96,8 @@ class GpuStep:
         self.bk, self.bp, self.pk = t(inp["bk"]), t(inp["bp"]), t(inp["pk"])
         self.host = inp
         self.results = {}
+        self.learned = False
+        self.ws = {}
 
     def tensors(self):
         out = [self.bk, self.bp, self.pk]
@@ -110,6 +112,16 @@ class GpuStep:
             self.results[name] = tab.probe(self.pk, capacity=self.pk.numel())
             return
         q = self.q[name]
+        if self.learned:
+            # learned sizing (sketch + planner network) in one call, with the
+            # exact re-plan inside the call when the estimate overflows
+            if name not in self.ws:
+                self.ws[name] = rel._ws(rel.auto_ws_bytes(q), self.dev)
+            keys, aggs, plan = rel.groupby_auto(q, flags=rel.PLAN_LEARNED | rel.PLAN_SKETCH,
+                                                ws=self.ws[name])
+            self.results[name] = (keys, aggs)
+            self.results[name + ".plan"] = plan
+            return
         plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
         self.results[name] = rel.groupby(q, plan=plan)
         self.results[name + ".plan"] = plan
@@ -451,8 +463,12 @@ def main():
     ap.add_argument("--small", action="store_true", help="10x smaller workload (quick checks)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--learned", type=int, default=200,
+    ap.add_argument("--learned", type=int, default=2000,
                     help="instances of the learned-sizing comparison (0 = skip)")
+    ap.add_argument("--no-learned-step", action="store_true",
+                    help="skip the step timed with learned plans")
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the 1e8-row lineitem run and the host-link measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain comparison")
     args = ap.parse_args()
@@ -564,6 +580,11 @@ def main():
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, g, inp, stream, world, barrier, rows_step)
+    if rank == 0 and not args.no_learned_step:
+        line["learned_step"] = run_learned_step(args, g, stream, rows_step, ms_step)
+    if rank == 0 and not args.no_scale:
+        line["lineitem_1e8"] = run_lineitem_scale(args, dev, peak_gbs)
+        line["h2d_link"] = measure_h2d(dev)
     if rank == 0 and not args.no_cpu_baseline:
         t = time_oracle_parts(inp, sz, CPU_FRACS)
         v, _ = extrapolate(t, rows_full)
@@ -581,6 +602,119 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_learned_step(args, g, stream, rows_step, plain_ms_step):
+    """The same step with every group-by planned by the learned form (sketch +
+    planner network; an overflowing estimate is re-planned exactly inside the
+    call), device-timed like the plain step, results compared part by part
+    with the plain step's."""
+    import torch
+
+    from paper_2608_13696_gb300 import planner, rel
+
+    if not os.path.exists(planner.DEFAULT_WEIGHTS):
+        return {"skipped": "no trained planner network"}
+    planner.use_default()
+    plain = {p: g.results[p] for p in ("lineitem", "zipf", "fourkeys")}
+    g.learned = True
+    try:
+        for _ in range(max(1, args.warmup)):
+            for p in PARTS:
+                g.part(p)
+        torch.cuda.synchronize()
+        parts = {p: 0.0 for p in PARTS}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for p in PARTS:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g.part(p)
+                b.record(stream)
+                b.synchronize()
+                parts[p] += a.elapsed_time(b) / args.steps
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        mismatches, fell_back = 0, []
+        for p, (k0, a0) in plain.items():
+            k1, a1 = g.results[p]
+            s0, o0 = torch.sort(k0)
+            s1, o1 = torch.sort(k1)
+            same = torch.equal(s0, s1) and all(torch.equal(x[o0], y[o1]) for x, y in zip(a0, a1))
+            mismatches += not same
+            if g.results[p + ".plan"].flags & rel.PLAN_FELL_BACK:
+                fell_back.append(p)
+    finally:
+        g.learned = False
+    return {"value": rows_step / (ms / 1e3), "unit": "rows/s", "ms_per_step": ms,
+            "plain_ms_per_step": plain_ms_step, "speedup_vs_plain": plain_ms_step / ms,
+            "parts_ms": parts, "mismatches": mismatches, "fell_back": fell_back,
+            "plans": "learned sizing (sketch + network, exact re-plan on overflow) + sketch pins"}
+
+
+def run_lineitem_scale(args, dev, peak_gbs):
+    """The lineitem filter + group-by at 1e8 rows (3.8 GB, far above L2): the
+    fused kernel's stable roofline figure, device-timed over 5 launches."""
+    import torch
+
+    import synth
+    from paper_2608_13696_gb300 import rel
+    from paper_2608_13696_gb300.workloads import lineitem_query
+
+    n = 100_000_000 if not args.small else 10_000_000
+    li = synth.lineitem(n, seed=7)
+    q = lineitem_query(li)
+    q["cols"] = [torch.from_numpy(c).to(dev) for c in q["cols"]]
+    nbytes = sum(c.numel() * c.element_size() for c in q["cols"])
+    del li
+    plan = rel.plan_groupby(q, flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
+    for _ in range(3):
+        rel.groupby(q, plan=plan)
+    torch.cuda.synchronize()
+    rel.profile_start()
+    for _ in range(5):
+        rel.groupby(q, plan=plan)
+    torch.cuda.synchronize()
+    recs = rel.profile_stop()
+    kern = {}
+    for name, ms in recs:
+        kern.setdefault(name, []).append(ms)
+    main_k = max(kern, key=lambda k: sum(kern[k]))
+    ms = float(np.mean(kern[main_k]))
+    gbs = nbytes / (ms / 1e3) / 1e9
+    out = {"rows": n, "bytes": nbytes, "kernel": main_k, "ms_per_launch": ms, "algo_gbs": gbs,
+           "frac": gbs / peak_gbs, "frac_nominal": gbs / NOMINAL_HBM_GBS,
+           "rows_per_s": n / (ms / 1e3), "groups": int(plan.est_groups),
+           "plan": "exact distinct count + sketch pins (registers)"}
+    del q
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_h2d(dev):
+    """Pinned host -> device copy rate alone (1 GiB, best of 5), against which
+    the end-to-end figure's copies can be read."""
+    import torch
+
+    h = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    best = None
+    for _ in range(5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        d.copy_(h, non_blocking=True)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    del h, d
+    return {"bytes": 1 << 30, "ms": best, "gbs": (1 << 30) / (best / 1e3) / 1e9,
+            "how": "one cudaMemcpyAsync of 1 GiB from pinned host memory, best of 5"}
 
 
 def run_learned(args):

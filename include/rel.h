@@ -166,7 +166,7 @@ typedef struct {
   int32_t tile_rows;        /* rows per staged tile (256..2048, power of two); 0 = auto */
   int32_t n_stages;         /* staging ring depth (2..8); 0 = auto                    */
   int32_t part_bits;        /* REL_VAR_PARTITIONED: log2 of the partition count
-                               (4..13); smem_slots is then each partition's table */
+                               (4..14); smem_slots is then each partition's table */
   int32_t reserved;
 } rel_plan;
 
@@ -477,6 +477,34 @@ rel_status rel_batch_autotune(const rel_batch_groupby* gb, int32_t n_gb, const r
                               int32_t reps, void* ws, size_t ws_bytes, rel_batch_handle* handle,
                               rel_batch_config* best, float* ms, void* stream);
 
+/* ------------------------------------------------------------- sharding */
+
+/* Sharded group-by across G ranks (one GPU each): every rank aggregates its
+ * own rows (rel_groupby_agg), splits its partial groups by owner with this
+ * call, exchanges them (an all-to-all of the per-owner ranges), and merges
+ * the partials it owns with a second group-by (sum of sums, sum of counts,
+ * min of mins, max of maxes).  The path shards the rows (the paper profiles
+ * one GPU; its Sec. 6.1 notes multi-GPU underutilisation under skew); sum,
+ * count, min and max are exact in int64, so the merged groups equal the
+ * unsharded ones bit for bit.
+ *
+ * rel_shard_split: owner(k) = floor(h * world / 2^64), h = (k ^ 2^63) *
+ * 0xD1B54A32D192ED03 mod 2^64 (a multiplier independent of the table
+ * hashes).  Writes the n groups (keys[i], words[w][i]) to out_keys /
+ * out_words grouped by owner -- owner 0's groups first, then owner 1's, ...;
+ * order inside an owner's range unspecified -- and the number of groups per
+ * owner to counts_host[world] (after a stream sync).  keys, words, outputs:
+ * device int64 arrays of n; words / out_words: n_words (<= REL_MAX_AGGS)
+ * device pointers (host arrays).  ws: rel_shard_ws_bytes(world) device bytes.
+ * 1 <= world <= REL_SHARD_MAX_WORLD.  Returns REL_OK, REL_E_INVALID,
+ * REL_E_UNSUPPORTED (world out of range), REL_E_CAPACITY (ws too small),
+ * REL_E_CUDA. */
+#define REL_SHARD_MAX_WORLD 64
+uint64_t rel_shard_ws_bytes(int32_t world);
+rel_status rel_shard_split(const int64_t* keys, const int64_t* const* words, int32_t n_words,
+                           int64_t n, int32_t world, int64_t* out_keys, int64_t* const* out_words,
+                           int64_t* counts_host, void* ws, size_t ws_bytes, void* stream);
+
 /* ----------------------------------------------------------------- join */
 
 /* Handle to a built join table.  It lives in caller memory, points into the
@@ -497,9 +525,10 @@ typedef struct {
 } rel_join_probe_desc;
 
 /* Device bytes rel_join_build needs for n_build build rows: a 256-byte
- * header, next_pow2(2 * n_build) (at least 16) slots of 32 bytes (key,
- * payload, build row index: one sector, read by the probe with one load), and
- * a 16-byte side entry per build row for the key INT64_MIN. */
+ * header, next_pow2(2 * n_build) (at least 16) slots of 16 bytes (key, build
+ * row index), a copy of the payload column (8 bytes per build row, rounded up
+ * to 256 bytes) from which the probe gathers, and a 16-byte side entry per
+ * build row for the key INT64_MIN. */
 uint64_t rel_join_ws_bytes(int64_t n_build);
 
 /* Build (the paper's insert step): every build row j (key[j], payload[j])

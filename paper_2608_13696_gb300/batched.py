@@ -169,6 +169,7 @@ def measure(gb_inputs, join_inputs, reps: int = 3, autotune: bool = True,
         times.append(time.perf_counter() - t0)
     t_batch = float(np.median(times))
     batched_out = batch_outputs(b, counts, redo)
+    device = device_times(b, g, gb_inputs, join_inputs, counts)
     # plain
     times = []
     plain_out = None
@@ -186,4 +187,43 @@ def measure(gb_inputs, join_inputs, reps: int = 3, autotune: bool = True,
             "batched_with_plan_rows_per_s": rows / (t_batch + t_plan),
             "plain_rows_per_s": rows / t_plain, "speedup": t_plain / t_batch,
             "speedup_with_plan": t_plain / (t_batch + t_plan),
-            "fallbacks": len(redo), "mismatches": mismatches, "config": tuned or b.config}
+            "fallbacks": len(redo), "mismatches": mismatches, "config": tuned or b.config,
+            "device": device}
+
+
+def device_times(b: rel.Batch, graph, gb_inputs, join_inputs, counts) -> dict:
+    """Device time of the graph replay alone (CUDA events, no read-back, no
+    fallback re-runs) and of each persistent launch (one direct run with the
+    library's launch timing), with their algorithmic bytes: launch A reads
+    every group-by row (key + value) and every build row (key + payload);
+    launch B reads every probe key and writes every pair (16 bytes) and every
+    group (key + two aggregates)."""
+    sync = torch.cuda.synchronize
+    ms = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sync()
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    rel.profile_start()
+    b.run()
+    sync()
+    kern = {}
+    for name, t in rel.profile_stop():
+        kern[name] = kern.get(name, 0.0) + t
+    ng = len(gb_inputs)
+    a_bytes = sum(k.numel() * (k.element_size() + 8) for k, _ in gb_inputs) + \
+        sum(bk.numel() * 16 for bk, _, _ in join_inputs)
+    b_bytes = sum(pk.numel() * 8 for _, _, pk in join_inputs) + \
+        16 * sum(counts[ng:]) + 24 * sum(counts[:ng])
+    out = {"replay_ms": float(np.median(ms)), "kernels_ms": kern,
+           "batch_a_bytes": a_bytes, "batch_b_bytes": b_bytes}
+    if kern.get("batch_a"):
+        out["batch_a_gbs"] = a_bytes / (kern["batch_a"] / 1e3) / 1e9
+    if kern.get("batch_b"):
+        out["batch_b_gbs"] = b_bytes / (kern["batch_b"] / 1e3) / 1e9
+    return out

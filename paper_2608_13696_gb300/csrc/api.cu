@@ -461,6 +461,10 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   }
   rel_status r;
   if (!plan->tile_rows && gb_ppass_stream_eligible(p, shape, plan->n_hot)) {
+    // one CTA per SM: fewer (partition, CTA) write cursors, so the partly
+    // written record sectors stay in L2 until they fill
+    p.fixed_grid = (uint32_t)relhost::device_sms() < PART_MAX_GRID ? (uint32_t)relhost::device_sms()
+                                                                   : PART_MAX_GRID;
     if ((r = gb_launch_ppass_stream(p, shape, false, st))) return r;
     if ((r = gb_launch_part_scan(p, st))) return r;
     if ((r = gb_launch_ppass_stream(p, shape, true, st))) return r;
@@ -991,8 +995,8 @@ struct JoinLayout {
 JoinLayout join_layout(int64_t n_build) {
   JoinLayout L;
   L.slots = next_pow2((uint64_t)(2 * n_build < 16 ? 16 : 2 * n_build));
-  L.bytes = HEADER_BYTES + L.slots * sizeof(JoinSlot) +
-            (uint64_t)(n_build > 0 ? n_build : 1) * sizeof(JoinVal);
+  const uint64_t nb = (uint64_t)(n_build > 0 ? n_build : 1);
+  L.bytes = HEADER_BYTES + L.slots * sizeof(JoinSlot) + align_up(nb * 8, 256) + nb * sizeof(JoinVal);
   return L;
 }
 
@@ -1001,8 +1005,10 @@ JoinParams join_params(const rel_join_table* t) {
   uint8_t* ws = (uint8_t*)t->ws;
   const uint64_t slots = (uint64_t)t->slots;
   p.hdr = (WsHeader*)ws;
+  const uint64_t nb = (uint64_t)(t->n_build > 0 ? t->n_build : 1);
   p.slots = (JoinSlot*)(ws + HEADER_BYTES);
-  p.side = (JoinVal*)(ws + HEADER_BYTES + sizeof(JoinSlot) * slots);
+  p.pay = (long long*)(ws + HEADER_BYTES + sizeof(JoinSlot) * slots);
+  p.side = (JoinVal*)((uint8_t*)p.pay + align_up(nb * 8, 256));
   p.log2_slots = t->log2_slots;
   return p;
 }
@@ -1357,7 +1363,7 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   if (plan->variant == REL_VAR_PARTITIONED &&
       (plan->part_bits < 4 || plan->part_bits > PART_MAX_BITS || plan->smem_slots < 256 ||
        plan->smem_slots > SHARED_MAX_SLOTS || d->n_rows >= (1ll << 32)))
-    return set_error("group-by: partitioned plans need part_bits in [4, 13], smem_slots in "
+    return set_error("group-by: partitioned plans need part_bits in [4, 14], smem_slots in "
                      "[256, 4096] and fewer than 2^32 rows"),
            REL_E_INVALID;
   const uint64_t need_all = plan_ws_bytes(plan, d->n_aggs, d->n_rows);

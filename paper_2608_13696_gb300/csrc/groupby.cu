@@ -948,7 +948,8 @@ __device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, uns
   gtab_update<S>(p, ek, x);
 }
 
-constexpr int PA_R = 4;  // record groups in flight per warp in the aggregation pass
+constexpr int PA_R = 4;        // record groups in flight per warp in the aggregation pass
+constexpr int PA_COMBINE = 6;  // lanes of the first key above which they are combined first
 
 // Pass 3: each CTA aggregates whole partitions in a shared-memory table of
 // p.smem_slots slots and writes their groups straight to the output (warp
@@ -987,12 +988,12 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
     if (threadIdx.x == 0) ovf = nch > 1;
     __syncthreads();
     {
-      // each warp takes 32 consecutive records at a time; the rows of the
-      // warp's first key (under skew, usually the partition's heavy key) are
-      // combined in registers first (0 is every word's identity) and applied
-      // once, the other rows go to the table one by one
-      // PA_R groups of 32 records per warp are loaded before any is used
-      // (the pass is bound by load latency)
+      // each warp takes 32 consecutive records at a time, PA_R such groups
+      // loaded before any is used (the pass is bound by load latency); when
+      // more than PA_COMBINE lanes hold the warp's first key (under skew,
+      // usually the partition's heavy key) its rows are combined in registers
+      // first (0 is every word's identity) and applied once, every other row
+      // goes to the table on its own
       const int warp = threadIdx.x >> 5;
       for (unsigned long long b00 = beg + (unsigned long long)warp * 32 * PA_R; b00 < end;
            b00 += (unsigned long long)GB_BLOCK * PA_R) {
@@ -1022,7 +1023,9 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
         const uint64_t key = __shfl_sync(0xffffffffu, ek, ld);
         const bool mine = valid && ek == key;
         const unsigned m = __ballot_sync(0xffffffffu, mine);
-        const bool combine = __popc(m) > 1;  // uniform across the warp
+        // combining costs ~3 x 5 shuffle rounds; worth it only when many lanes
+        // would otherwise serialise on one shared-memory word
+        const bool combine = __popc(m) > PA_COMBINE;  // uniform across the warp
         if (combine) {
           // the first key's words over its lanes; its count is the lanes'
           // number (word 1 of the key/value shapes counts rows)

@@ -29,7 +29,7 @@ struct alignas(16) PartRec {
   unsigned long long ek;
   long long val;
 };
-constexpr int PART_MAX_BITS = 13;  // at most 8192 partitions
+constexpr int PART_MAX_BITS = 14;  // at most 16384 partitions
 constexpr int PART_CHUNKS = 16;    // CTAs that may share one oversized partition
 
 // Row shapes.  The specialised ones fix column types and aggregate kinds at

@@ -5,14 +5,15 @@
 // matches), with the payload brought in by a separate gather (Sec. 7,
 // Table 9), and finds count and retrieve bound by instruction issue and
 // memory latency on GH200.  Here the table is an open-addressing array at
-// load <= 1/2 whose 32-byte slots hold the key, the payload and the build row
-// index together -- 2^21 slots (64 MB) for a 10^6-row build side, which stays
-// in the GB300's L2 while the probe keys stream from HBM -- so a probe reads
-// key and payload with one 256-bit load (the gather is fused into the probe:
-// one L2 request per probed slot).  Every probe row's first slot is loaded
-// before any is resolved, probe keys arrive in 16-byte vector loads, and each
-// warp compacts its lanes' matches with a ballot / popc and reserves output
-// space with one atomic.
+// load <= 1/2 of 16-byte slots (key, build row index) plus the table's own
+// copy of the payload column -- 32 MB + 8 MB for a 10^6-row build side, small
+// enough to stay in the GB300's L2 (whose random-access sweet spot is below
+// ~64 MB) while the probe keys stream from HBM with evict-first loads and the
+// outputs leave with streaming stores.  The payload gather is fused into the
+// probe.  Every probe row's first slot is loaded before any is resolved,
+// probe keys arrive in 16-byte vector loads, and each warp compacts its
+// lanes' matches with a ballot / popc and reserves output space with one
+// atomic.
 #include "join.cuh"
 
 namespace rel {
@@ -21,21 +22,18 @@ namespace {
 
 constexpr int J_BLOCK = 256;
 
-// One slot, marked evict-last in L2 so that the table outlives the streamed
-// probe keys (evict-first) and the streamed outputs.
-__device__ __forceinline__ void ld_slot(const JoinSlot* p, uint64_t& ek, int64_t& payload,
-                                        int32_t& bidx) {
-  unsigned long long a, b, c, d;
+// One slot (key, build row index), marked evict-last in L2 so that the table
+// outlives the streamed probe keys (evict-first) and the streamed outputs.
+__device__ __forceinline__ void ld_slot(const JoinSlot* p, uint64_t& ek, int32_t& bidx) {
+  unsigned long long a, b;
   asm volatile(
       "{\n\t.reg .b64 pol;\n\t"
       "createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
-      "ld.global.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], pol;\n\t}"
-      : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+      "ld.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], pol;\n\t}"
+      : "=l"(a), "=l"(b)
       : "l"(p));
-  (void)d;
   ek = a;
-  payload = (int64_t)b;
-  bidx = (int32_t)(uint32_t)c;
+  bidx = (int32_t)(uint32_t)b;
 }
 
 __global__ void __launch_bounds__(J_BLOCK) join_build_k(const __grid_constant__ JoinParams p,
@@ -48,6 +46,7 @@ __global__ void __launch_bounds__(J_BLOCK) join_build_k(const __grid_constant__ 
        j += (int64_t)gridDim.x * J_BLOCK) {
     const uint64_t ek = (uint64_t)__ldg((const long long*)keys + j) ^ KEY_FLIP;
     const long long pay = __ldg((const long long*)payload + j);
+    p.pay[j] = pay;  // the table's copy of the payload column
     if (ek == 0) {  // INT64_MIN: side list
       const unsigned long long pos = atomicAdd(&p.hdr->n_side, 1ull);
       p.side[pos] = JoinVal{pay, (int32_t)j, 0};
@@ -60,7 +59,6 @@ __global__ void __launch_bounds__(J_BLOCK) join_build_k(const __grid_constant__ 
       if (cur == 0) {
         cur = atomicCAS(&p.slots[s].ek, 0ull, (unsigned long long)ek);
         if (cur == 0) {
-          p.slots[s].payload = pay;
           p.slots[s].bidx = (int32_t)j;
           placed = true;
           break;
@@ -92,10 +90,13 @@ __device__ __forceinline__ bool next_match(const JoinParams& p, uint64_t ek, boo
   const uint64_t mask = (1ull << p.log2_slots) - 1;
   for (uint64_t i = 0; i <= mask; ++i) {
     uint64_t k;
-    ld_slot(p.slots + s, k, pay, bidx);
+    ld_slot(p.slots + s, k, bidx);
     if (k == 0) return false;
     s = (s + 1) & mask;
-    if (k == ek) return true;
+    if (k == ek) {
+      pay = p.pay[bidx];
+      return true;
+    }
   }
   return false;
 }
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(J_BLOCK) join_probe_fast_k(const __grid_consta
         slow[q] = valid && (ek[g + q] == 0 || !unique);
         s[q] = slot_of(ek[g + q], p.log2_slots);
         k[q] = 0;
-        if (valid && !slow[q]) ld_slot(p.slots + s[q], k[q], pay[q], bidx[q]);
+        if (valid && !slow[q]) ld_slot(p.slots + s[q], k[q], bidx[q]);
       }
 #pragma unroll
       for (int q = 0; q < J_G; ++q) {
@@ -163,11 +164,15 @@ __global__ void __launch_bounds__(J_BLOCK) join_probe_fast_k(const __grid_consta
         if (row[g + q] < n && !slow[q]) {
           for (uint64_t step = 0; step <= mask && k[q] != 0 && k[q] != ek[g + q]; ++step) {
             s[q] = (s[q] + 1) & mask;
-            ld_slot(p.slots + s[q], k[q], pay[q], bidx[q]);
+            ld_slot(p.slots + s[q], k[q], bidx[q]);
           }
           hit[q] = k[q] == ek[g + q];
         }
       }
+      // the payload gather of every hit of the group
+#pragma unroll
+      for (int q = 0; q < J_G; ++q)
+        if (EMIT && hit[q]) pay[q] = __ldg(p.pay + bidx[q]);
       unsigned m[J_G];
       unsigned total = 0;
 #pragma unroll

@@ -14,20 +14,22 @@ struct alignas(16) JoinVal {
 };
 
 // One slot of the single-call join table: the stored key (key ^ KEY_FLIP,
-// 0 = empty), the build row's payload and index -- one 32-byte sector, so a
-// probe reads key and payload with one 256-bit load.
-struct alignas(32) JoinSlot {
+// 0 = empty) and the build row index -- 16 bytes, read with one 128-bit
+// load.  The payload is gathered by that index from the table's own copy of
+// the payload column, so the L2-resident part of a 10^6-row table is 32 MB of
+// slots + 8 MB of payloads.
+struct alignas(16) JoinSlot {
   unsigned long long ek;
-  long long payload;
   int32_t bidx;
   int32_t pad;
-  long long pad2;
 };
-static_assert(sizeof(JoinSlot) == 32, "one sector per slot");
+static_assert(sizeof(JoinSlot) == 16, "two slots per sector");
 
-// Workspace layout: [WsHeader 256 B][slots x 32 B][side n_build x 16 B]
+// Workspace layout: [WsHeader 256 B][slots x 16 B][payload n_build x 8 B]
+//                   [side n_build x 16 B]
 struct JoinParams {
   JoinSlot* slots;
+  long long* pay;    // payload of build row j at pay[j]
   JoinVal* side;     // build rows whose key is INT64_MIN
   WsHeader* hdr;
   int32_t log2_slots;

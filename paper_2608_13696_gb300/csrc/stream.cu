@@ -294,10 +294,10 @@ __global__ void __launch_bounds__(ST_BLOCK, 6) gb_stream_k(const __grid_constant
 // into the spill table.  INT64_MIN rows go to the side accumulator in pass 2.
 // Both passes cover the rows in the same order with the same grid, so every
 // CTA's positions are exactly the ones it counted.
-constexpr int SP_BLOCK = 256;
+constexpr int SP_BLOCK = 512;
 
 template <class KT, int NA, bool PIN, bool SCATTER>
-__global__ void __launch_bounds__(SP_BLOCK) gb_ppass_stream_k(const __grid_constant__ GbParams p) {
+__global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_constant__ GbParams p) {
   extern __shared__ __align__(16) uint8_t sm[];
   constexpr int PM = pin_max<NA>();
   uint64_t* pk = (uint64_t*)sm;

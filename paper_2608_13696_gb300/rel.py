@@ -190,7 +190,9 @@ EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join
            "rel_mlp_ws_bytes", "rel_mlp_backward", "rel_mlp_adamw", "rel_planner_set",
            "rel_batch_ws_bytes", "rel_batch_prepare", "rel_batch_run", "rel_batch_results",
            "rel_batch_autotune", "rel_sketch_batched", "rel_sketch_batched_ws_bytes",
-           "rel_plan_learned_rule", "rel_plan_size_batched", "rel_plan_size_batched_ws_bytes"]
+           "rel_plan_learned_rule", "rel_plan_size_batched", "rel_plan_size_batched_ws_bytes",
+           "rel_shard_ws_bytes", "rel_shard_split"]
+SHARD_MAX_WORLD = 64
 SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
 
@@ -283,6 +285,12 @@ def load(build_if_stale: bool = True):
         L.rel_plan_size_batched.restype = i32
         L.rel_plan_size_batched.argtypes = [ctypes.POINTER(GroupByDesc), i32, u32, vp,
                                             ctypes.c_size_t, ctypes.POINTER(Plan), vp]
+        L.rel_shard_ws_bytes.restype = u64
+        L.rel_shard_ws_bytes.argtypes = [i32]
+        L.rel_shard_split.restype = i32
+        L.rel_shard_split.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), i32, i64, i32, vp,
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(i64), vp,
+                                      ctypes.c_size_t, vp]
         PG, PJ = ctypes.POINTER(BatchGroupBy), ctypes.POINTER(BatchJoinC)
         PC, PH = ctypes.POINTER(BatchConfig), ctypes.POINTER(BatchHandle)
         L.rel_batch_ws_bytes.restype = u64
@@ -457,6 +465,27 @@ def groupby_auto(q: dict, flags: int = 0, capacity: int | None = None,
 
 def auto_ws_bytes(q: dict) -> int:
     return int(load().rel_groupby_auto_ws_bytes(ctypes.byref(_Desc(q).d)))
+
+
+def shard_split(keys: torch.Tensor, words: list, world: int, stream=None):
+    """rel_shard_split: the groups (keys, words) regrouped by owner rank.
+    Returns (keys, [words], counts per owner)."""
+    L = load()
+    n = keys.numel()
+    for t in [keys, *words]:
+        if t.dtype != torch.int64 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("keys and words must be contiguous CUDA int64 tensors of one length")
+    dev = keys.device
+    out_k = torch.empty(max(1, n), dtype=torch.int64, device=dev)[:n]
+    out_w = [torch.empty(max(1, n), dtype=torch.int64, device=dev)[:n] for _ in words]
+    nw = len(words)
+    wp = (ctypes.c_void_p * max(1, nw))(*[w.data_ptr() for w in words])
+    op = (ctypes.c_void_p * max(1, nw))(*[w.data_ptr() for w in out_w])
+    counts = (ctypes.c_int64 * max(1, world))()
+    ws = _ws(L.rel_shard_ws_bytes(world), dev)
+    _check(L.rel_shard_split(keys.data_ptr(), wp, nw, n, world, out_k.data_ptr(), op, counts,
+                             ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out_k, out_w, [int(counts[r]) for r in range(world)]
 
 
 # ---------------------------------------------------------- planner network

@@ -44,9 +44,10 @@ def test_version_and_counters(L):
 def test_ws_sizes(L):
     assert L.rel_groupby_ws_bytes(16, 4) == 256 + 16 * 8 * 5
     assert L.rel_groupby_ws_bytes(1 << 20, 2) == 256 + (1 << 20) * 24
-    # join: next_pow2(2n) slots x 32 B (key, payload, build index) + n x 16 B side list
-    assert L.rel_join_ws_bytes(1_000_000) == 256 + (1 << 21) * 32 + 1_000_000 * 16
-    assert L.rel_join_ws_bytes(0) == 256 + 16 * 32 + 16
+    # join: next_pow2(2n) slots x 16 B (key, build index) + the payload copy (n x 8 B,
+    # rounded up to 256 B) + n x 16 B side list
+    assert L.rel_join_ws_bytes(1_000_000) == 256 + (1 << 21) * 16 + 8_000_000 + 1_000_000 * 16
+    assert L.rel_join_ws_bytes(0) == 256 + 16 * 16 + 256 + 16
 
 
 def _desc(n_rows=100, **over):
