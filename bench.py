@@ -727,9 +727,11 @@ def run_learned(args):
         return {"skipped": "no trained planner network"}
     n = args.learned if not args.small else min(args.learned, 20)
     r = planner.evaluate(range(1_000_000, 1_000_000 + n), with_labels=False, log_every=0,
-                         rows_hi=50_000_000 if not args.small else 5_000_000)
+                         rows_hi=50_000_000 if not args.small else 5_000_000, with_rows=False)
     r.pop("per_instance", None)
     r["timing"] = "wall clock per instance (plan + run + result count), inputs resident, L2 flushed"
+    r["workload"] = (f"{n} unseen planner-workload instances (rows log-U[1e6, 5e7], uniform / "
+                     f"Zipf 0.5, 1.0, 1.5 / clustered keys, domains log-U[10, 1e8])")
     return r
 
 

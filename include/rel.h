@@ -438,8 +438,9 @@ typedef struct {
   int32_t block;           /* threads per CTA: 128, 256 or 512 */
   int32_t items;           /* rows per thread per tile: 4, 8 or 16 */
   int32_t probe_width;     /* threads probing the global table together: 1, 2, 4, 8 */
-  int32_t smem_max_groups; /* group-bys with est_groups <= this (at most 512)
-                              pre-aggregate each tile in shared memory; 0 = none */
+  int32_t smem_max_groups; /* group-bys with est_groups <= this (at most 2048)
+                              pre-aggregate each work item (up to 32 tiles) in
+                              shared memory; 0 = none */
 } rel_batch_config;
 
 /* Host handle filled by rel_batch_prepare (opaque, caller-owned). */

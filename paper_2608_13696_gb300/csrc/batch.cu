@@ -89,13 +89,13 @@ __device__ __forceinline__ void side_update(const BatchGb& g, BatchStatus* st, c
   red_words(g, st->side_aggs, x);
 }
 
-// One thread: insert-or-accumulate encoded words into the global table.
-__device__ __forceinline__ void global_update(const BatchGb& g, BatchStatus* st, uint64_t ek,
-                                              const Words& x) {
+// One thread: insert-or-accumulate encoded words into the global table,
+// starting from slot s whose content cur was already loaded.
+__device__ __forceinline__ void global_resolve(const BatchGb& g, BatchStatus* st, uint64_t ek,
+                                               uint64_t s, uint64_t cur, const Words& x) {
   const uint64_t mask = (1ull << g.log2_slots) - 1;
-  uint64_t s = slot_of(ek, g.log2_slots);
   for (uint32_t i = 0; i < g.max_probe; ++i) {
-    uint64_t cur = ld_relaxed(g.tkeys + s);
+    if (i) cur = ld_relaxed(g.tkeys + s);
     if (cur == 0) {
       cur = atomicCAS((unsigned long long*)(g.tkeys + s), 0ull, (unsigned long long)ek);
       if (cur == 0) cur = ek;
@@ -108,6 +108,12 @@ __device__ __forceinline__ void global_update(const BatchGb& g, BatchStatus* st,
     if ((i & 31) == 31 && ld_relaxed_u32(&st->overflow)) return;  // already overflowed
   }
   atomicOr(&st->overflow, 1u);
+}
+
+__device__ __forceinline__ void global_update(const BatchGb& g, BatchStatus* st, uint64_t ek,
+                                              const Words& x) {
+  const uint64_t s = slot_of(ek, g.log2_slots);
+  global_resolve(g, st, ek, s, ld_relaxed(g.tkeys + s), x);
 }
 
 // W threads probe together: each reads one slot of a W-slot window; a key
@@ -165,11 +171,12 @@ __device__ __noinline__ void global_update_coop(const BatchGb& g, BatchStatus* s
   }
 }
 
+// One tile of B x ITEMS rows starting at row r0: each row goes to the
+// shared-memory table (when the instance has one) or the global table.
 template <int ITEMS, int W>
-__device__ __forceinline__ void gb_tile(const BatchGb& g, BatchStatus* st, long long t,
+__device__ __forceinline__ void gb_rows(const BatchGb& g, BatchStatus* st, long long r0,
                                         uint64_t* smk, unsigned long long* sma) {
   const int B = blockDim.x;
-  const long long r0 = t * (long long)B * ITEMS;
   uint64_t ek[ITEMS];
   int64_t vv[ITEMS];
   bool ok[ITEMS];
@@ -179,19 +186,15 @@ __device__ __forceinline__ void gb_tile(const BatchGb& g, BatchStatus* st, long 
     ok[j] = r < g.n_rows;
     int64_t k = 0, v = 0;
     if (ok[j]) {
-      k = g.key_type == REL_I32 ? (int64_t)__ldg((const int*)g.keys + r)
-                                : (int64_t)__ldg((const long long*)g.keys + r);
-      if (g.vals) v = (int64_t)__ldg((const long long*)g.vals + r);
+      k = g.key_type == REL_I32 ? (int64_t)__ldcs((const int*)g.keys + r)
+                                : (int64_t)__ldcs((const long long*)g.keys + r);
+      if (g.vals) v = (int64_t)__ldcs((const long long*)g.vals + r);
     }
     ek[j] = (uint64_t)k ^ KEY_FLIP;
     vv[j] = v;
   }
   if (g.smem_slots) {
-    // tile pre-aggregation in a shared-memory table, then one global update
-    // per distinct key of the tile
     const uint32_t S = (uint32_t)g.smem_slots, A = (uint32_t)g.n_aggs;
-    for (uint32_t i = threadIdx.x; i < S * (1 + A); i += B) smk[i] = 0;
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       if (!ok[j]) continue;
@@ -219,6 +222,50 @@ __device__ __forceinline__ void gb_tile(const BatchGb& g, BatchStatus* st, long 
       }
       if (!placed) global_update(g, st, ek[j], x);
     }
+    return;
+  }
+  if (W == 1) {
+    // every row's first slot is read before any row is resolved: ITEMS
+    // independent L2 round trips in flight per thread instead of one
+    uint64_t gs[ITEMS], gk[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      gs[j] = slot_of(ek[j], g.log2_slots);
+      gk[j] = (ok[j] && ek[j] != 0) ? ld_relaxed(g.tkeys + gs[j]) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      if (!ok[j]) continue;
+      const Words x = row_words(g, vv[j]);
+      if (ek[j] == 0)
+        side_update(g, st, x);
+      else
+        global_resolve(g, st, ek[j], gs[j], gk[j], x);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) global_update_coop<W>(g, st, ek[j], vv[j], ok[j]);
+  }
+}
+
+// Work item t of a group-by: g.span consecutive tiles.  With a shared-memory
+// table the item pre-aggregates all its rows there (cleared once, flushed to
+// the global table once, one update per distinct key).
+template <int ITEMS, int W>
+__device__ __forceinline__ void gb_tile(const BatchGb& g, BatchStatus* st, long long t,
+                                        uint64_t* smk, unsigned long long* sma) {
+  const int B = blockDim.x;
+  const long long T = (long long)B * ITEMS;
+  const long long first = t * (long long)g.span;
+  const long long last = (g.n_rows + T - 1) / T < first + g.span ? (g.n_rows + T - 1) / T
+                                                                 : first + g.span;
+  const uint32_t S = (uint32_t)g.smem_slots, A = (uint32_t)g.n_aggs;
+  if (S) {
+    for (uint32_t i = threadIdx.x; i < S * (1 + A); i += B) smk[i] = 0;
+    __syncthreads();
+  }
+  for (long long k = first; k < last; ++k) gb_rows<ITEMS, W>(g, st, k * T, smk, sma);
+  if (S) {
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < S; s += B) {
       const uint64_t k = smk[s];
@@ -229,21 +276,6 @@ __device__ __forceinline__ void gb_tile(const BatchGb& g, BatchStatus* st, long 
       global_update(g, st, k, x);
     }
     __syncthreads();
-    return;
-  }
-  if (W == 1) {
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      if (!ok[j]) continue;
-      const Words x = row_words(g, vv[j]);
-      if (ek[j] == 0)
-        side_update(g, st, x);
-      else
-        global_update(g, st, ek[j], x);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) global_update_coop<W>(g, st, ek[j], vv[j], ok[j]);
   }
 }
 

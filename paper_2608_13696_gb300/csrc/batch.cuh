@@ -8,7 +8,12 @@
 namespace rel {
 
 constexpr int BATCH_MAX_AGGS = 4;
-constexpr int BATCH_MAX_SMEM_SLOTS = 1024;
+constexpr int BATCH_MAX_SMEM_SLOTS = 4096;
+// Rows of one group-by work item: up to this many tiles of blockDim x ITEMS
+// rows, so the per-item costs (the work counter, the instance search, the
+// descriptor copy, clearing and flushing a shared-memory table) are paid once
+// per ~64K rows rather than once per tile.
+constexpr int BATCH_GB_SPAN = 32;
 
 // One group-by instance as the kernels see it.
 struct alignas(16) BatchGb {
@@ -26,7 +31,7 @@ struct alignas(16) BatchGb {
   int32_t log2_slots;
   int32_t smem_slots;  // 0: every row updates the global table
   uint32_t max_probe;
-  int32_t pad;
+  int32_t span;        // tiles of blockDim x ITEMS rows per work item
 };
 
 // One join partition: its build side, its probe side, its table and outputs.

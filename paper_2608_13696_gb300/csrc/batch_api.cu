@@ -152,7 +152,8 @@ rel_status validate_config(const rel_batch_config* c) {
   if (c->probe_width != 1 && c->probe_width != 2 && c->probe_width != 4 && c->probe_width != 8)
     return set_error("batch: probe_width must be 1, 2, 4 or 8"), REL_E_INVALID;
   if (c->smem_max_groups < 0 || c->smem_max_groups > BATCH_MAX_SMEM_SLOTS / 2)
-    return set_error("batch: smem_max_groups must be in [0, 512]"), REL_E_INVALID;
+    return set_error("batch: smem_max_groups must be in [0, %d]", BATCH_MAX_SMEM_SLOTS / 2),
+           REL_E_INVALID;
   return REL_OK;
 }
 
@@ -211,9 +212,10 @@ rel_status prepare(const rel_batch_groupby* gb, int32_t n_g, const rel_batch_joi
     d.log2_slots = log2u((uint64_t)g.slots);
     d.smem_slots = smem_slots_for(g, *cfg);
     d.max_probe = (uint32_t)std::min<int64_t>(g.slots, 4096);
+    d.span = BATCH_GB_SPAN;
     smem_bytes = std::max(smem_bytes, d.smem_slots * 8 * (1 + g.n_aggs));
     std::memcpy(at(L.off_gb) + sizeof(BatchGb) * i, &d, sizeof d);
-    gbt[i + 1] = gbt[i] + (g.n_rows + T - 1) / T;
+    gbt[i + 1] = gbt[i] + (g.n_rows + T * BATCH_GB_SPAN - 1) / (T * BATCH_GB_SPAN);
     gct[i + 1] = gct[i] + (g.slots + T - 1) / T;
   }
   long long* jbt = (long long*)at(L.off_jbt);

@@ -81,8 +81,34 @@ def _time_plan(qc, plan, reps, flush, ws, cap, give_up_ms=float("inf")):
     return float(np.median(times))
 
 
+# share of the runs that are filtered, packed-key inputs (the lineitem shape:
+# date filter of varying selectivity, (flag, status) key, five aggregates)
+LINEITEM_SHARE = 0.05
+LINEITEM_ROWS = (1_000_000, 20_000_000)
+
+
+def _lineitem_instance(seed: int, dev):
+    """A filtered packed-key run: lineitem-like columns (host generator) of
+    log-uniform rows, keeping date <= a seeded threshold."""
+    import synth
+    from . import workloads
+
+    rng = np.random.default_rng(seed)
+    lo, hi = LINEITEM_ROWS
+    n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+    li = synth.lineitem(n, seed=seed)
+    q = workloads.lineitem_query(li, date_hi=int(rng.integers(100, 2527)))
+    q["cols"] = [torch.from_numpy(c).to(dev) for c in q["cols"]]
+    return q, {"rows": n, "domain": 6, "fam": 9, "s": 0.0}
+
+
+def _is_lineitem(seed: int) -> bool:
+    return np.random.default_rng((seed, 7)).random() < LINEITEM_SHARE
+
+
 def collect(seeds, out: str, reps: int = 3, rows_lo: int = 1_000_000,
-            rows_hi: int = 50_000_000, log_every: int = 200, save_every: int = 2000) -> dict:
+            rows_hi: int = 50_000_000, log_every: int = 200, save_every: int = 2000,
+            with_lineitem: bool = False) -> dict:
     from synth import gpu as G
 
     dev = torch.device("cuda")
@@ -91,24 +117,37 @@ def collect(seeds, out: str, reps: int = 3, rows_lo: int = 1_000_000,
     ws = None
     t_start = time.time()
     for i, seed in enumerate(seeds):
-        inst = G.instance(seed, rows_lo=rows_lo, rows_hi=rows_hi)
-        k, v = G.instance_kv(inst, dev)
-        qc = kv_query(k, v)
+        if with_lineitem and _is_lineitem(seed):
+            qc, inst = _lineitem_instance(seed, dev)
+            k = v = None
+        else:
+            inst = G.instance(seed, rows_lo=rows_lo, rows_hi=rows_hi)
+            k, v = G.instance_kv(inst, dev)
+            qc = kv_query(k, v)
+        n_aggs = len(qc["aggs"])
         s = rel.sketch(qc)
         exact = rel.plan_groupby(qc, flags=rel.PLAN_EXACT)
         ndv = max(1, int(exact.est_groups))
         row = []
         for var in VARIANTS:
-            plan = rel.plan_groupby(qc, flags=rel.PLAN_SKETCH | rel.plan_force(var),
-                                    groups_hint=ndv)
-            need = int(rel.load().rel_plan_ws_bytes(plan, 4, inst["rows"]))
+            try:
+                plan = rel.plan_groupby(qc, flags=rel.PLAN_SKETCH | rel.plan_force(var),
+                                        groups_hint=ndv)
+            except rel.RelError as e:  # e.g. no partitioned variant for packed keys
+                if e.status != rel.REL_E_UNSUPPORTED:
+                    raise
+                row.append(float("inf"))
+                continue
+            need = int(rel.load().rel_plan_ws_bytes(plan, n_aggs, inst["rows"]))
             if ws is None or ws.numel() < need:
+                ws = None
+                torch.cuda.empty_cache()
                 ws = torch.empty(need, dtype=torch.uint8, device=dev)
             try:
                 best = min(row) if row else float("inf")
                 row.append(_time_plan(qc, plan, reps, flush, ws, ndv + 1, give_up_ms=2 * best))
-            except rel.RelError as e:  # a variant that cannot run at this size
-                if e.status != rel.REL_E_OVERFLOW:
+            except rel.RelError as e:  # a variant that cannot run on this input
+                if e.status not in (rel.REL_E_OVERFLOW, rel.REL_E_UNSUPPORTED):
                     raise
                 print(f"collect: seed {seed} variant {var}: {e}", file=sys.stderr)
                 row.append(float("inf"))
@@ -238,8 +277,10 @@ def _sorted(keys, aggs):
 
 
 def evaluate(seeds, weights: str = DEFAULT_WEIGHTS, rows_lo: int = 1_000_000,
-             rows_hi: int = 50_000_000, with_labels: bool = True, log_every: int = 200) -> dict:
-    """The learned plan vs the exact pre-pass (and vs sizing for n_rows)."""
+             rows_hi: int = 50_000_000, with_labels: bool = True, log_every: int = 200,
+             with_rows: bool = True) -> dict:
+    """The learned plan vs the exact pre-pass (and, with_rows, vs sizing for
+    n_rows)."""
     from synth import gpu as G
 
     dev = torch.device("cuda")
@@ -247,8 +288,9 @@ def evaluate(seeds, weights: str = DEFAULT_WEIGHTS, rows_lo: int = 1_000_000,
     flush = _Flush(dev)
     ws = None
     forms = {"learned": rel.PLAN_LEARNED | rel.PLAN_SKETCH,
-             "exact": rel.PLAN_EXACT | rel.PLAN_SKETCH,
-             "rows": rel.PLAN_SKETCH}
+             "exact": rel.PLAN_EXACT | rel.PLAN_SKETCH}
+    if with_rows:
+        forms["rows"] = rel.PLAN_SKETCH
     tot = {f: 0.0 for f in forms}
     rows_total = 0
     mismatches, fallbacks = 0, 0
@@ -275,7 +317,9 @@ def evaluate(seeds, weights: str = DEFAULT_WEIGHTS, rows_lo: int = 1_000_000,
             if f == "learned" and plan.flags & rel.PLAN_FELL_BACK:
                 fallbacks += 1
         (ke, ae), pe = res["exact"]
-        for f in ("learned", "rows"):
+        for f in forms:
+            if f == "exact":
+                continue
             (kf, af), _ = res[f]
             if not (torch.equal(kf, ke) and all(torch.equal(x, y) for x, y in zip(af, ae))):
                 mismatches += 1
@@ -299,8 +343,9 @@ def evaluate(seeds, weights: str = DEFAULT_WEIGHTS, rows_lo: int = 1_000_000,
     out = {"instances": len(per), "rows": rows_total, "mismatches": mismatches,
            "fallbacks": fallbacks,
            "ms_total": tot, "speedup_vs_exact": tot["exact"] / tot["learned"],
-           "speedup_vs_rows": tot["rows"] / tot["learned"],
            "rows_per_s": {f: rows_total / (tot[f] * 1e-3) for f in forms}}
+    if with_rows:
+        out["speedup_vs_rows"] = tot["rows"] / tot["learned"]
     if with_labels and per:
         err = np.array([math.log2(max(1, r["est_learned"]) / 1.25) - math.log2(max(1, r["groups"]))
                         for r in per])
@@ -324,6 +369,8 @@ def main(argv=None):
     c.add_argument("--reps", type=int, default=3)
     c.add_argument("--rows-lo", type=int, default=1_000_000)
     c.add_argument("--rows-hi", type=int, default=50_000_000)
+    c.add_argument("--with-lineitem", action="store_true",
+                   help="make about 5 %% of the runs filtered packed-key (lineitem-like) inputs")
     t = sub.add_parser("train")
     t.add_argument("runs", nargs="+")
     t.add_argument("--out", required=True)
@@ -342,7 +389,8 @@ def main(argv=None):
     e.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     if a.cmd == "collect":
-        collect(_parse_range(a.seeds), a.out, reps=a.reps, rows_lo=a.rows_lo, rows_hi=a.rows_hi)
+        collect(_parse_range(a.seeds), a.out, reps=a.reps, rows_lo=a.rows_lo, rows_hi=a.rows_hi,
+                with_lineitem=a.with_lineitem)
     elif a.cmd == "train":
         print(json.dumps(train(a.runs, a.out, epochs=a.epochs, batch=a.batch, lr=a.lr, wd=a.wd,
                                seed=a.seed, ckpt=a.ckpt)))

@@ -1,47 +1,150 @@
-"""Small cases of the hot kernels, one launch each, for profiler captures.
+"""Small cases of the library's kernels for profiler captures, one case per
+run, each launching the kernels of interest a few times at most.
 
-    python -m paper_2608_13696_gb300.profile_cases
+    python -m paper_2608_13696_gb300.profile_cases CASE
 
-runs, on 5e7-row inputs: the exact distinct-count pre-pass and a partitioned
-group-by with the sample sketch over Zipf(1.1) key/value rows; a streaming
-group-by with pinned keys over four-key rows; a join table of 1e6 keys probed
-with 4e6 keys.  Small enough for a full-section capture of each launch.
+CASE (inputs seeded and synthetic, as in the bench):
+  distinct  exact distinct count of 5e7 Zipf(1.1) keys (distinct_k)
+  part      partitioned group-by of 5e7 Zipf(1.1) key/value rows with the
+            sample sketch's pins (histogram, scan, scatter, aggregation,
+            compaction)
+  stream    streaming group-by of 5e7 four-key rows with pinned keys (gb_stream)
+  join      join build of 1e6 unique keys and probe of 1.6e7 keys (90 % hits)
+  lineitem  fused filter + group-by of 2e7 lineitem rows: exact count (staged
+            key set), sketch, register-privatised aggregation, compaction
+  mlp       planner network forward, backward and AdamW on a batch of 256
+  batch     a batch of 512 group-bys and 64 join partitions (the batched
+            workload's recipe, rows divided by 8): the two persistent launches
+  shard     owner split of 2e6 partial groups over 8 ranks
+Sizes keep every case below a few GB of device memory, with inputs above the
+129 MB L2 where the kernel streams.
 """
 from __future__ import annotations
 
 import sys
 
+import numpy as np
 import torch
 
 from . import rel
 
 
-def kv_query(k, v):
-    return {"cols": [k, v], "keys": [0], "preds": [],
-            "aggs": [("sum", 1, []), ("count", 1, []), ("min", 1, []), ("max", 1, [])]}
+def kv_query(k, v, ops=("sum", "count", "min", "max")):
+    return {"cols": [k, v], "keys": [0], "preds": [], "aggs": [(o, 1, []) for o in ops]}
 
 
-def main(n: int = 50_000_000) -> None:
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def case_distinct(n=50_000_000):
     import synth
 
     zk, zv = synth.zipf_kv(n, seed=0)
-    q = kv_query(torch.from_numpy(zk).cuda(), torch.from_numpy(zv).cuda())
-    del zk, zv
-    ex = rel.plan_groupby(q, flags=rel.PLAN_EXACT)
+    q = kv_query(_cuda(zk), _cuda(zv), ops=("count",))
+    return rel.plan_groupby(q, flags=rel.PLAN_EXACT).est_groups
+
+
+def case_part(n=50_000_000):
+    import synth
+
+    zk, zv = synth.zipf_kv(n, seed=0)
+    q = kv_query(_cuda(zk), _cuda(zv))
     p = rel.plan_groupby(q, flags=rel.plan_force(rel.VAR_PARTITIONED) | rel.PLAN_SKETCH,
-                         groups_hint=ex.est_groups)
-    rel.groupby(q, plan=p, capacity=ex.est_groups + 1)
+                         groups_hint=3_300_000)
+    k, _ = rel.groupby(q, plan=p, capacity=4_000_000)
+    return k.numel()
+
+
+def case_stream(n=50_000_000):
+    import synth
+
     fk, fv = synth.few_keys_kv(n, n_keys=4, seed=0)
-    q4 = kv_query(torch.from_numpy(fk).cuda(), torch.from_numpy(fv).cuda())
-    p4 = rel.plan_groupby(q4, flags=rel.PLAN_SKETCH | rel.plan_force(rel.VAR_GLOBAL), groups_hint=4)
-    rel.groupby(q4, plan=p4, capacity=8)
-    bk, bp = synth.join_build(1_000_000, seed=0)
-    pk, _ = synth.join_probe(4_000_000, 1_000_000, seed=0)
-    t = rel.JoinTable(torch.from_numpy(bk).cuda(), torch.from_numpy(bp).cuda())
-    t.probe(torch.from_numpy(pk).cuda(), capacity=4_000_000)
-    torch.cuda.synchronize()
-    print("ok", ex.est_groups)
+    q = kv_query(_cuda(fk), _cuda(fv))
+    p = rel.plan_groupby(q, flags=rel.PLAN_SKETCH, groups_hint=4)
+    k, _ = rel.groupby(q, plan=p, capacity=8)
+    return k.numel()
+
+
+def case_join(nb=1_000_000, np_=16_000_000):
+    import synth
+
+    bk, bp = synth.join_build(nb, seed=0)
+    pk, _ = synth.join_probe(np_, nb, seed=0)
+    t = rel.JoinTable(_cuda(bk), _cuda(bp))
+    return t.probe(_cuda(pk), capacity=np_)[0].numel()
+
+
+def case_lineitem(n=20_000_000):
+    import synth
+
+    from .workloads import lineitem_query
+
+    q = lineitem_query(synth.lineitem(n, seed=0))
+    q["cols"] = [_cuda(c) for c in q["cols"]]
+    p = rel.plan_groupby(q, flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
+    k, _ = rel.groupby(q, plan=p)
+    return k.numel()
+
+
+def case_mlp(batch=256):
+    g = torch.Generator().manual_seed(0)
+    p = (torch.rand(rel.MLP_PARAMS, generator=g) * 0.2 - 0.1).cuda()
+    x = torch.rand(batch, rel.MLP_IN, generator=g).cuda()
+    bf = torch.empty(rel.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    rel.mlp_round(p, bf)
+    acts = torch.empty((batch, 2 * rel.MLP_HIDDEN), device="cuda")
+    y = rel.mlp_forward(bf, p, x, acts)
+    t = torch.rand(batch, generator=g).cuda() * 20
+    v = torch.randint(0, 3, (batch,), generator=g, dtype=torch.int32).cuda()
+    grad = torch.empty_like(p)
+    loss = torch.empty(1, device="cuda")
+    rel.mlp_backward(bf, x, acts, y, t, v, grad, loss)
+    m, s = torch.zeros_like(p), torch.zeros_like(p)
+    rel.mlp_adamw(p, bf, m, s, grad, 1)
+    return float(loss.item())
+
+
+def case_batch():
+    from synth import gpu as G
+
+    from . import batched
+
+    r = G.batch_recipe(0, n_groupby=512, n_join=64)
+    for x in r["groupby"]:
+        x["rows"] = max(1, x["rows"] // 8)
+    for x in r["join"]:
+        x["probe"] = max(1, x["probe"] // 8)
+    gb, jn = G.batch_inputs(r)
+    est = [min(k.numel(), 100_000) for k, _ in gb]
+    sizes = [(e, 1 << max(4, (2 * e - 1).bit_length()),
+              rel.VAR_SMEM if e <= 512 else rel.VAR_GLOBAL) for e in est]
+    b = batched.make_batch(gb, jn, sizes).prepare((512, 4, 1, 512))
+    b.run()
+    counts, _ = b.results()
+    return sum(counts)
+
+
+def case_shard(n=2_000_000, world=8):
+    g = torch.Generator().manual_seed(0)
+    k = torch.randint(-(1 << 62), 1 << 62, (n,), generator=g).cuda()
+    w = [torch.randint(-1000, 1000, (n,), generator=g).cuda() for _ in range(4)]
+    _, _, counts = rel.shard_split(k, w, world)
+    return counts
+
+
+CASES = {"distinct": case_distinct, "part": case_part, "stream": case_stream,
+         "join": case_join, "lineitem": case_lineitem, "mlp": case_mlp, "batch": case_batch,
+         "shard": case_shard}
+
+
+def main(argv) -> None:
+    rel.load()
+    for name in argv or list(CASES):
+        out = CASES[name]()
+        torch.cuda.synchronize()
+        print(name, "ok", out)
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 50_000_000)
+    main(sys.argv[1:])

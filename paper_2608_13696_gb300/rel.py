@@ -704,7 +704,7 @@ class JoinTable:
 DEFAULT_BATCH_CONFIG = (256, 8, 1, 512)
 # the tuner's search space: block x items x probe width x shared-memory placement
 BATCH_SEARCH = [(b, it, w, sm) for b in (128, 256, 512) for it in (4, 8, 16)
-                for w in (1, 2, 4, 8) for sm in (0, 512)]
+                for w in (1, 2, 4, 8) for sm in (0, 512, 2048)]
 
 
 class Batch:

@@ -82,7 +82,7 @@ def test_bad_partition_plan_rejected():
     keys, vals = synth.zipf_kv(50_000, seed=17, n_ranks=20_000)
     qc = query_to_cuda(oracle.kv_query(keys, vals))
     plan = rel.plan_groupby(qc, flags=rel.PLAN_EXACT)
-    plan.part_bits = 14
+    plan.part_bits = 15  # above the 16384-partition limit
     with pytest.raises(rel.RelError) as e:
         rel.groupby(qc, plan=plan)
     assert e.value.status == rel.REL_E_INVALID
