@@ -11,10 +11,11 @@
 //   * exact sample statistics: distinct keys, keys seen once, runs of equal
 //     consecutive keys within each window, minimum and maximum key;
 //   * the 32 most frequent keys (count descending, key ascending).
-// Keys are sorted in shared memory with a bitonic network (warp-local stages
-// between warp barriers, CTA barriers only for the long distances); distinct
-// keys and their counts come from the run starts of the sorted keys, listed
-// with a prefix sum, so no thread walks a long run of equal keys.
+// Distinct keys and their counts come from a shared-memory hash table of
+// sample positions (no sort); the top keys from a histogram of the counts
+// (the cut at the 32nd largest count) and a bitonic sort of only the keys
+// counted at least that often -- a handful for a skewed sample, every key
+// when all are seen once.
 #include "sketch.cuh"
 
 namespace rel {
@@ -23,6 +24,7 @@ namespace {
 
 constexpr int SK_THREADS = 1024;
 constexpr int SK_N = SKETCH_SAMPLE;  // 4096
+constexpr int SK_TAB = 2 * SK_N;     // hash table entries (load <= 1/2)
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -39,25 +41,14 @@ __device__ __forceinline__ int64_t read_col(const SketchParams& p, int c, int64_
   }
 }
 
-// Bitonic sort of SK_N (a, b) pairs in shared memory by less.  A stage with
-// compare distance below 64 only pairs elements inside one aligned 128-element
-// block, so warp w sorts block w on its own between two __syncwarp()s; only
-// the 21 stages with distance >= 64 need the whole CTA (of 78 in all).
+// Bitonic sort of the first n (a power of two, <= SK_N) pairs, a CTA
+// barrier per stage (the candidate lists are short for skewed samples).
 template <class Less>
-__device__ void bitonic(int64_t* a, int64_t* b, Less less) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  bool prev_block = true;
-  for (int size = 2; size <= SK_N; size <<= 1) {
+__device__ void bitonic_n(int64_t* a, int64_t* b, int n, Less less) {
+  for (int size = 2; size <= n; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      const bool block = stride >= 64;
-      if (block || prev_block) __syncthreads();
-      else __syncwarp();
-      prev_block = block;
-#pragma unroll
-      for (int r = 0; r < SK_N / 2 / SK_THREADS; ++r) {
-        // pair number t: block stages spread the pairs over the CTA, warp
-        // stages keep warp w on the pairs of its own 128 elements
-        const int t = block ? threadIdx.x + r * SK_THREADS : 64 * warp + lane + 32 * r;
+      __syncthreads();
+      for (int t = threadIdx.x; t < n / 2; t += SK_THREADS) {
         const int lo = 2 * t - (t & (stride - 1));
         const int hi = lo + stride;
         const bool up = (lo & size) == 0;
@@ -109,11 +100,14 @@ __device__ int block_scan(int v, int* total) {
 // One CTA sketches one input.
 __device__ __forceinline__ void sketch_body(const SketchParams& p, DevSketch* out) {
   extern __shared__ int64_t sk_dyn[];
-  int64_t* key = sk_dyn;        // [SK_N] sampled keys, then sorted
-  int64_t* aux = sk_dyn + SK_N;  // [SK_N] 0 kept / 1 dropped, then counts
-  int* start = (int*)(sk_dyn + 2 * SK_N);  // [SK_N + 1] positions of the distinct keys
+  int64_t* key = sk_dyn;          // [SK_N] sampled keys
+  int64_t* aux = sk_dyn + SK_N;    // [SK_N] 0 kept / 1 dropped, then candidate counts
+  int64_t* key2 = sk_dyn + 2 * SK_N;  // [SK_N] candidate keys
+  int* tab = (int*)(sk_dyn + 3 * SK_N);  // [SK_TAB] 1 + sample position of a key
+  int* tcnt = tab + SK_TAB;              // [SK_TAB] its count
+  int* start = tcnt + SK_TAB;            // [SK_N + 4] count histogram
   __shared__ unsigned int hll[256];
-  __shared__ int n_kept, n_ndv, n_single, n_runs;
+  __shared__ int n_kept, n_ndv, n_single, n_runs, s_cut;
   __shared__ unsigned long long kmin_u, kmax_u;  // order-mapped (k ^ 2^63)
 
   const int64_t n = p.n_rows;
@@ -121,7 +115,7 @@ __device__ __forceinline__ void sketch_body(const SketchParams& p, DevSketch* ou
   const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < 256; i += SK_THREADS) hll[i] = 0;
   if (threadIdx.x == 0) {
-    n_kept = n_single = n_runs = 0;
+    n_kept = n_ndv = n_single = n_runs = 0;
     kmin_u = ~0ull;
     kmax_u = 0ull;
   }
@@ -195,56 +189,105 @@ __device__ __forceinline__ void sketch_body(const SketchParams& p, DevSketch* ou
     }
     if (runs) atomicAdd(&n_runs, runs);
   }
-  // sort by (dropped, key): kept keys first, ascending
-  bitonic(aux, key, [](int64_t a0, int64_t b0, int64_t a1, int64_t b1) {
-    return a0 != a1 ? a0 < a1 : b0 < b1;
-  });
   const int m = n_kept;
-  // distinct keys: the run starts of the sorted prefix, listed in order by a
-  // prefix sum (thread t owns positions 4t .. 4t + 3); a key's count is the
-  // distance to the next start
+  // distinct keys and their counts: a shared-memory hash table of sample
+  // positions (load <= 1/2), entry = 1 + the position of the key's first
+  // insert; equal keys meet at the same entry and add to its count
   constexpr int PER = SK_N / SK_THREADS;
-  const int i0 = PER * threadIdx.x;
-  int here = 0;
-#pragma unroll
-  for (int o = 0; o < PER; ++o) {
-    const int i = i0 + o;
-    here += (i < m && (i == 0 || key[i] != key[i - 1])) ? 1 : 0;
-  }
-  int ndv = 0;
-  int pos = block_scan(here, &ndv);
-#pragma unroll
-  for (int o = 0; o < PER; ++o) {
-    const int i = i0 + o;
-    if (i < m && (i == 0 || key[i] != key[i - 1])) start[pos++] = i;
-  }
-  if (threadIdx.x == 0) {
-    start[ndv] = m;
-    n_ndv = ndv;
+  for (int i = threadIdx.x; i < SK_TAB; i += SK_THREADS) {
+    tab[i] = 0;
+    tcnt[i] = 0;
   }
   __syncthreads();
-  int single = 0;
 #pragma unroll
-  for (int o = 0; o < PER; ++o) {
-    const int i = i0 + o;
-    aux[i] = 0;  // count at a run start (below), 0 elsewhere
+  for (int r = 0; r < PER; ++r) {
+    const int j = threadIdx.x + r * SK_THREADS;
+    if (j >= S || aux[j]) continue;
+    const int64_t k = key[j];
+    uint32_t t = (uint32_t)(splitmix64((uint64_t)k) >> 32) & (SK_TAB - 1);
+    for (int probe = 0; probe < SK_TAB; ++probe) {
+      int cur = tab[t];
+      if (cur == 0) {
+        cur = atomicCAS(&tab[t], 0, j + 1);
+        if (cur == 0) {
+          atomicAdd(&tcnt[t], 1);
+          break;
+        }
+      }
+      if (key[cur - 1] == k) {
+        atomicAdd(&tcnt[t], 1);
+        break;
+      }
+      t = (t + 1) & (SK_TAB - 1);
+    }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < ndv; r += SK_THREADS) {
-    const int c = start[r + 1] - start[r];
-    aux[start[r]] = c;
+  // distinct and single keys; histogram of the counts (bins 1 .. SK_N)
+  int* hist = start;  // [SK_N + 1]
+  for (int i = threadIdx.x; i <= SK_N; i += SK_THREADS) hist[i] = 0;
+  __syncthreads();
+  int nd = 0, single = 0;
+  for (int i = threadIdx.x; i < SK_TAB; i += SK_THREADS) {
+    const int c = tcnt[i];
+    if (c == 0) continue;
+    ++nd;
     single += c == 1;
+    atomicAdd(&hist[c], 1);
   }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) single += __shfl_xor_sync(0xffffffffu, single, o);
+  for (int o = 16; o; o >>= 1) {
+    nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    single += __shfl_xor_sync(0xffffffffu, single, o);
+  }
+  if (lane == 0 && nd) atomicAdd(&n_ndv, nd);
   if (lane == 0 && single) atomicAdd(&n_single, single);
   __syncthreads();
-  // top keys: sort by (count descending, key ascending); non-starts (count 0) last
-  bitonic(aux, key, [](int64_t c0, int64_t k0, int64_t c1, int64_t k1) {
+  const int ndv = n_ndv;
+  // cut: the SKETCH_TOP-th largest count (every key counted at least that
+  // often is a candidate, so ties at the cut are all present); thread t owns
+  // the bins 4t + 1 .. 4t + 4
+  int mine = 0;
+#pragma unroll
+  for (int o = 1; o <= PER; ++o) mine += hist[PER * threadIdx.x + o];
+  int all = 0;
+  const int below = block_scan(mine, &all);  // keys counted <= 4t times
+  int above = all - below - mine;             // keys counted > 4t + 4 times
+  if (threadIdx.x == 0) s_cut = 1;
+  __syncthreads();
+  if (ndv > SKETCH_TOP) {
+#pragma unroll
+    for (int o = PER; o >= 1; --o) {
+      const int c = PER * threadIdx.x + o, h = hist[c];
+      if (above < SKETCH_TOP && above + h >= SKETCH_TOP) s_cut = c;
+      above += h;
+    }
+  }
+  __syncthreads();
+  const int cut = s_cut;
+  // the candidates (count >= cut), listed with a prefix sum, then sorted by
+  // (count descending, key ascending); the padding sorts last
+  int here = 0;
+  for (int i = PER * 2 * threadIdx.x; i < PER * 2 * (threadIdx.x + 1); ++i) here += tcnt[i] >= cut;
+  int n_cand = 0;
+  int pos = block_scan(here, &n_cand);
+  for (int i = PER * 2 * threadIdx.x; i < PER * 2 * (threadIdx.x + 1); ++i) {
+    if (tcnt[i] >= cut && tcnt[i] > 0) {
+      aux[pos] = tcnt[i];
+      key2[pos] = key[tab[i] - 1];
+      ++pos;
+    }
+  }
+  int n2 = 2;
+  while (n2 < n_cand) n2 <<= 1;
+  for (int i = n_cand + threadIdx.x; i < n2; i += SK_THREADS) {
+    aux[i] = -1;
+    key2[i] = 0;
+  }
+  bitonic_n(aux, key2, n2, [](int64_t c0, int64_t k0, int64_t c1, int64_t k1) {
     return c0 != c1 ? c0 > c1 : k0 < k1;
   });
   for (int i = threadIdx.x; i < SKETCH_TOP; i += SK_THREADS) {
-    out->top_key[i] = i < ndv ? key[i] : 0;
+    out->top_key[i] = i < ndv ? key2[i] : 0;
     out->top_count[i] = i < ndv ? (int32_t)aux[i] : 0;
   }
   for (int i = threadIdx.x; i < 256; i += SK_THREADS) out->hll[i] = (uint8_t)hll[i];
@@ -274,7 +317,7 @@ __global__ void __launch_bounds__(SK_THREADS) sketch_many_k(const SketchParams* 
 
 rel_status sketch_many_launch(const SketchParams* ps, DevSketch* outs, int n, cudaStream_t st) {
   if (n <= 0) return REL_OK;
-  const int smem = 2 * SK_N * (int)sizeof(int64_t) + (SK_N + 4) * (int)sizeof(int);
+  const int smem = 3 * SK_N * (int)sizeof(int64_t) + (2 * SK_TAB + SK_N + 4) * (int)sizeof(int);
   cudaError_t e0 =
       cudaFuncSetAttribute(sketch_many_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e0 != cudaSuccess) return relhost::cuda_fail(e0, "cudaFuncSetAttribute(sketch)");
@@ -286,7 +329,7 @@ rel_status sketch_many_launch(const SketchParams* ps, DevSketch* outs, int n, cu
 }
 
 rel_status sketch_launch(const SketchParams& p, DevSketch* out, cudaStream_t st) {
-  const int smem = 2 * SK_N * (int)sizeof(int64_t) + (SK_N + 4) * (int)sizeof(int);
+  const int smem = 3 * SK_N * (int)sizeof(int64_t) + (2 * SK_TAB + SK_N + 4) * (int)sizeof(int);
   cudaError_t e0 = cudaFuncSetAttribute(sketch_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e0 != cudaSuccess) return relhost::cuda_fail(e0, "cudaFuncSetAttribute(sketch)");
   relhost::launch_begin(relhost::K_SKETCH, st);

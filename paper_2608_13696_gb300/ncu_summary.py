@@ -3,6 +3,7 @@ it reads captures taken on a GB300 with `ncu ... -o FILE`).
 
     python -m paper_2608_13696_gb300.ncu_summary [--traffic FILE] \\
         CAPTURE.ncu-rep=ID:UNITS:UNIT[:ALGO_BYTES] ...
+    python -m paper_2608_13696_gb300.ncu_summary --launches LAUNCHES.csv
 
 ID is the kernel's name in bench.py's kernel table (e.g. gb_part_scatter),
 UNITS how many rows (or probes, groups, ...) the captured launch processed,
@@ -136,11 +137,43 @@ def sha1(rel_path: str) -> str:
     return hashlib.sha1(open(os.path.join(ROOT, rel_path), "rb").read()).hexdigest()
 
 
+def launch_table(csv_path: str, skip_prefixes=("at::", "void at::")) -> str:
+    """Markdown table of an `ncu --metrics gpu__time_duration.sum --csv
+    --log-file` launch list: per kernel, launches, total time, share of the
+    library's kernel time, grid x block (torch's own kernels left out)."""
+    rows = [r for r in csv.reader(open(csv_path)) if len(r) > 10]
+    hdr = rows[0]
+    ki, vi, ui = hdr.index("Kernel Name"), hdr.index("Metric Value"), hdr.index("Metric Unit")
+    gi, bi = hdr.index("Grid Size"), hdr.index("Block Size")
+    agg = {}
+    for r in rows[1:]:
+        name = r[ki]
+        if name.startswith(skip_prefixes):
+            continue
+        t = float(r[vi].replace(",", "")) * _SCALE.get(r[ui], 1e-9)
+        short = name.replace("(anonymous namespace)::", "").replace("unnamed>::", "")
+        short = short.replace("void ", "").replace("rel::", "").split("(")[0]
+        a = agg.setdefault(short, [0, 0.0, r[gi] + " x " + r[bi]])
+        a[0] += 1
+        a[1] += t
+    total = sum(v[1] for v in agg.values()) or 1.0
+    lines = ["| kernel | launches | total us | share | grid x block |", "|---|---|---|---|---|"]
+    for k, (n, t, gb) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        lines.append(f"| `{k}` | {n} | {t * 1e6:.1f} | {100 * t / total:.1f} % | {gb} |")
+    lines.append(f"\nTotal {total * 1e6:.1f} us over {sum(v[0] for v in agg.values())} library launches.")
+    return "\n".join(lines)
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(prog="python -m paper_2608_13696_gb300.ncu_summary")
-    ap.add_argument("captures", nargs="+", help="FILE.ncu-rep=ID:UNITS:UNIT[:ALGO_BYTES]")
+    ap.add_argument("captures", nargs="*", help="FILE.ncu-rep=ID:UNITS:UNIT[:ALGO_BYTES]")
     ap.add_argument("--traffic", default=None, help="JSON record for bench.py")
+    ap.add_argument("--launches", default=None, help="launch-list CSV to tabulate")
     a = ap.parse_args(argv)
+    if a.launches:
+        print(launch_table(a.launches))
+        if not a.captures:
+            return 0
     record = {"note": "DRAM bytes (read + write) and issued warp instructions per unit from one "
                       "ncu capture per kernel (paper_2608_13696_gb300.profile_cases); bench.py "
                       "scales them by its own launch's units and drops a record once one of "
