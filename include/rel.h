@@ -130,6 +130,9 @@ typedef struct {
 /* Set in plan->flags by rel_groupby_auto when the first plan overflowed and
  * the call re-planned with the exact pre-pass. */
 #define REL_PLAN_FELL_BACK 0x10000u
+/* Set in plan->flags by a REL_PLAN_LEARNED plan that a full-data HyperLogLog
+ * sized (see rel_plan_size). */
+#define REL_PLAN_HLL_SIZED 0x20000u
 /* Test hook for the device-side wait limit, not for production use.  Set in
  * plan->flags before rel_groupby_agg: the staged kernel's consumers never hand
  * a shared-memory stage back to its producer, so once a CTA's ring has gone
@@ -186,8 +189,14 @@ typedef struct {
  *      rel_sketch, then the registered planner network (rel_planner_set) on
  *      its features; est_groups = max(ceil(1.25 * 2^(y0 + 1)), sample distinct
  *      keys), the variant is the network's most likely one that the
- *      descriptor supports.  Needs rel_sketch_ws_bytes() + 2048 bytes of ws
- *      and returns REL_E_INVALID when no network is registered.  An estimate
+ *      descriptor supports.  For one int32 / int64 key without a filter,
+ *      at least 2^22 rows, and a sample whose distinct keys were more than
+ *      3/4 seen once (a long tail the sample cannot size), one streaming
+ *      pass of a full-data HyperLogLog (4096 registers) gives est = its
+ *      estimate x 1.25 instead, and the variant follows the rule by group
+ *      count; plan->flags then has REL_PLAN_HLL_SIZED.  Needs
+ *      rel_sketch_ws_bytes() + 18432 bytes of ws and returns REL_E_INVALID
+ *      when no network is registered.  An estimate
  *      can be too low: rel_groupby_agg then returns REL_E_OVERFLOW
  *      (rel_groupby_auto re-plans exactly).
  *    flags & REL_PLAN_SKETCH (with any of the above): also run rel_sketch and
@@ -344,6 +353,20 @@ rel_status rel_plan_learned_rule(const rel_sketch_info* info, const float* y, in
 uint64_t rel_plan_size_batched_ws_bytes(int32_t n);
 rel_status rel_plan_size_batched(const rel_groupby_desc* descs, int32_t n, uint32_t flags,
                                  void* ws, size_t ws_bytes, rel_plan* plans, void* stream);
+
+/* HyperLogLog of every key of one int32 / int64 column (no filter): the
+ * learned planner's full-data check for long tails.  p = 12: 4096 registers;
+ * h = fmix64(key ^ 2^63) (the MurmurHash3 64-bit finalizer), register h >> 52,
+ * value = leading zeros of the low 52 bits + 1 (53 when they are all zero);
+ * estimate as Flajolet, Fusy, Gandouet and Meunier (2007) with the
+ * small-range correction (standard error 1.04 / 64).  The paper has no
+ * planner; this is a sizing step of the learned form.  keys: device array of
+ * n; ws: rel_key_hll_ws_bytes() device bytes; regs_host: host uint32[4096];
+ * syncs the stream.  Returns REL_OK, REL_E_INVALID, REL_E_CAPACITY,
+ * REL_E_CUDA. */
+uint64_t rel_key_hll_ws_bytes(void);
+rel_status rel_key_hll(const void* keys, int32_t key_type, int64_t n, void* ws, size_t ws_bytes,
+                       uint32_t* regs_host, double* estimate, void* stream);
 
 /* ---------------------------------------------------- planner network */
 

@@ -182,6 +182,49 @@ def hll_estimate(registers) -> float:
     return float(e)
 
 
+_U64 = np.uint64
+
+
+def _fmix64(k: np.ndarray) -> np.ndarray:
+    """MurmurHash3's 64-bit finalizer (Appleby), on uint64 arrays (wrapping)."""
+    k = k.copy()
+    k ^= k >> _U64(33)
+    k *= _U64(0xFF51AFD7ED558CCD)
+    k ^= k >> _U64(33)
+    k *= _U64(0xC4CEB9FE1A85EC53)
+    k ^= k >> _U64(33)
+    return k
+
+
+def _clz64(x: np.ndarray) -> np.ndarray:
+    """Leading zero bits of each uint64 (64 for zero), by halving."""
+    x = x.copy()
+    n = np.zeros(x.shape, np.int64)
+    for s in (32, 16, 8, 4, 2, 1):
+        top = x >> _U64(64 - s)
+        z = top == 0
+        n += np.where(z, s, 0)
+        x = np.where(z, x << _U64(s), x)
+    n += (x == 0).astype(np.int64)  # x was zero throughout
+    return n
+
+
+def key_hll(keys, p: int = 12):
+    """HyperLogLog registers (2^p) of every key of one int32 / int64 column and
+    their estimate (Flajolet, Fusy, Gandouet & Meunier 2007, with the
+    small-range correction): h = fmix64(key ^ 2^63) over the key's 64-bit
+    two's-complement bits, register = top p bits of h, value = leading zeros
+    of the remaining 64 - p bits + 1 (65 - p when they are all zero)."""
+    k = np.asarray(keys).astype(np.int64).view(np.uint64) ^ _U64(1 << 63)
+    h = _fmix64(k)
+    idx = (h >> _U64(64 - p)).astype(np.int64)
+    rest = h << _U64(p)
+    rank = np.where(rest == 0, 65 - p, _clz64(rest) + 1)
+    regs = np.zeros(1 << p, np.uint32)
+    np.maximum.at(regs, idx, rank.astype(np.uint32))
+    return regs, hll_estimate(regs)
+
+
 def join(build_keys, payload, probe_keys):
     """Inner equi-join bag.  Returns (probe_idx int32, build_idx int32,
     payload int64) sorted by (probe_idx, build_idx)."""
@@ -202,26 +245,5 @@ def join_count(build_keys, probe_keys) -> int:
     return int(_L().orc_join_count(bk.ctypes.data, len(bk), pk.ctypes.data, len(pk)))
 
 
-def lineitem_query(li: dict, date_hi: int = 2430) -> dict:
-    """The fused filter + group-by over lineitem-like columns: keep date <= date_hi,
-    group by (flag, status), sum(qty), sum(price), sum(price*(100-disc)),
-    sum(price*(100-disc)*(100+tax)), count."""
-    cols = [li["flag"], li["status"], li["qty"], li["price"], li["disc"], li["tax"], li["date"]]
-    return {
-        "cols": cols,
-        "keys": [0, 1],
-        "preds": [(6, -(2**31), date_hi)],
-        "aggs": [
-            ("sum", 2, []),
-            ("sum", 3, []),
-            ("sum", 3, [(4, 100, -1)]),
-            ("sum", 3, [(4, 100, -1), (5, 100, 1)]),
-            ("count", 2, []),
-        ],
-    }
-
-
-def kv_query(keys, vals, ops=("sum", "count", "min", "max")) -> dict:
-    """Group-by of one int64 value column by one key column, no filter."""
-    return {"cols": [keys, vals], "keys": [0], "preds": [],
-            "aggs": [(o, 1, []) for o in ops]}
+# query descriptions of the benchmark workloads (shared with the GPU side)
+from synth.queries import kv_query, lineitem_query  # noqa: E402,F401

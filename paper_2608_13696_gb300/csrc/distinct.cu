@@ -13,8 +13,9 @@
 //    load, so almost every probe resolves in one L2 request and one compare
 //    chain (the paper's recommendation: fewer instructions per memory
 //    access);
-//  * a per-CTA direct-mapped filter of recently sent keys in shared memory
-//    drops the repeats of frequent keys before they reach the set;
+//  * an optional per-CTA direct-mapped filter of recently sent keys in shared
+//    memory drops repeats before they reach the set (off by default: the
+//    buckets of frequent keys come from L1 anyway);
 //  * every thread issues the bucket loads of several unfiltered rows before
 //    resolving any (memory-level parallelism), and the kernel runs at high
 //    occupancy so that many chunks of keys are in flight per SM;
@@ -24,6 +25,8 @@
 // inserts key k walks k's slots in the same order and stops at the first slot
 // holding k or claims the first empty one, so each distinct key is claimed
 // exactly once; the claims are the count.
+#include <cmath>
+
 #include "distinct.cuh"
 
 namespace rel {
@@ -209,6 +212,44 @@ __global__ void __launch_bounds__(DS_BLOCK, 3) distinct_k(const __grid_constant_
   }
 }
 
+// The MurmurHash3 64-bit finalizer (Appleby): a bijective mix of the key.
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xFF51AFD7ED558CCDull;
+  k ^= k >> 33;
+  k *= 0xC4CEB9FE1A85EC53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+template <class KT>
+__global__ void __launch_bounds__(DS_BLOCK) hll_k(const KT* __restrict__ keys, int64_t n,
+                                                  uint32_t* __restrict__ regs) {
+  __shared__ uint32_t r[HLL_REGS];
+  for (int i = threadIdx.x; i < HLL_REGS; i += DS_BLOCK) r[i] = 0;
+  __syncthreads();
+  constexpr int64_t CH = (int64_t)DS_BLOCK * DS_U;
+  const bool vec = (uintptr_t)keys % 16 == 0;
+  for (int64_t base = (int64_t)blockIdx.x * CH; base < n; base += (int64_t)gridDim.x * CH) {
+    uint64_t ek[DS_U];
+    uint32_t ok;
+    if (vec) load_chunk<KT, true>(keys, n, base, ek, ok);
+    else load_chunk<KT, false>(keys, n, base, ek, ok);
+#pragma unroll
+    for (int j = 0; j < DS_U; ++j) {
+      if (!(ok >> j & 1)) continue;
+      const uint64_t h = fmix64(ek[j]);
+      const uint64_t rest = h << HLL_P;
+      const uint32_t rank = rest == 0 ? (uint32_t)(65 - HLL_P) : (uint32_t)__clzll((long long)rest) + 1u;
+      uint32_t* x = r + (h >> (64 - HLL_P));
+      if (rank > *(volatile uint32_t*)x) atomicMax(x, rank);  // read first: most rows do not raise it
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < HLL_REGS; i += DS_BLOCK)
+    if (r[i]) atomicMax(regs + i, r[i]);
+}
+
 template <class KT, bool FILTER>
 rel_status launch(const DistinctParams& p, cudaStream_t st) {
   auto kern = distinct_k<KT, FILTER>;
@@ -231,6 +272,37 @@ rel_status launch(const DistinctParams& p, cudaStream_t st) {
 }
 
 }  // namespace
+
+rel_status hll_launch(const void* keys, int key_type, int64_t n, uint32_t* regs, cudaStream_t st) {
+  if (n <= 0) return REL_OK;
+  if (key_type != REL_I64 && key_type != REL_I32)
+    return relhost::set_error("hll: needs an int32 or int64 key"), REL_E_INVALID;
+  const int64_t chunks = (n + (int64_t)DS_BLOCK * DS_U - 1) / ((int64_t)DS_BLOCK * DS_U);
+  int64_t grid = (int64_t)relhost::device_sms() * 4;
+  if (grid > chunks) grid = chunks;
+  relhost::launch_begin(relhost::K_HLL, st);
+  if (key_type == REL_I64)
+    hll_k<int64_t><<<(int)grid, DS_BLOCK, 0, st>>>((const int64_t*)keys, n, regs);
+  else
+    hll_k<int32_t><<<(int)grid, DS_BLOCK, 0, st>>>((const int32_t*)keys, n, regs);
+  relhost::launch_end(relhost::K_HLL, st);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(hll)");
+}
+
+double hll_estimate(const uint32_t* regs) {
+  const double m = HLL_REGS;
+  double sum = 0.0;
+  int zeros = 0;
+  for (int i = 0; i < HLL_REGS; ++i) {
+    sum += std::ldexp(1.0, -(int)regs[i]);
+    zeros += regs[i] == 0;
+  }
+  const double alpha = 0.7213 / (1.0 + 1.079 / m);
+  double e = alpha * m * m / sum;
+  if (e <= 2.5 * m && zeros > 0) e = m * std::log(m / zeros);
+  return e;
+}
 
 rel_status distinct_launch(const DistinctParams& p, int key_type, cudaStream_t st) {
   if (p.n_rows == 0) return REL_OK;

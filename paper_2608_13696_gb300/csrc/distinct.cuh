@@ -30,4 +30,15 @@ inline size_t distinct_smem_bytes(uint32_t filter_slots) { return 8ull * filter_
 
 rel_status distinct_launch(const DistinctParams& p, int key_type, cudaStream_t st);
 
+// HyperLogLog over every key of one int32 / int64 column (p = 12: 4096
+// registers, caller-zeroed device uint32[4096]; register = top 12 bits of
+// fmix64(key ^ 2^63), value = leading zeros of the remaining 52 bits + 1,
+// 53 when they are all zero).  One streaming pass.
+constexpr int HLL_P = 12;
+constexpr int HLL_REGS = 1 << HLL_P;
+rel_status hll_launch(const void* keys, int key_type, int64_t n, uint32_t* regs, cudaStream_t st);
+// Cardinality estimate of HLL_REGS registers (Flajolet, Fusy, Gandouet and
+// Meunier 2007, with the small-range correction).
+double hll_estimate(const uint32_t* regs);
+
 }  // namespace rel

@@ -227,7 +227,8 @@ enum KernelId : int {
   K_BATCH_A = 13,
   K_BATCH_B = 14,
   K_GB_STREAM = 15,
-  K_COUNT_IDS = 16
+  K_HLL = 16,
+  K_COUNT_IDS = 17
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

@@ -51,6 +51,7 @@ SOURCES = {
     "batch_a": ["batch.cu", "batch_api.cu"],
     "batch_b": ["batch.cu", "batch_api.cu"],
     "shard_scatter": ["shard.cu"],
+    "hll": ["distinct.cu", "api.cu"],
 }
 
 METRICS = [

@@ -16,6 +16,7 @@ CASE (inputs seeded and synthetic, as in the bench):
   batch     a batch of 512 group-bys and 64 join partitions (the batched
             workload's recipe, rows divided by 8): the two persistent launches
   shard     owner split of 2e6 partial groups over 8 ranks
+  hll       full-data HyperLogLog of 5e7 Zipf(1.1) keys
 Sizes keep every case below a few GB of device memory, with inputs above the
 129 MB L2 where the kernel streams.
 """
@@ -133,9 +134,16 @@ def case_shard(n=2_000_000, world=8):
     return counts
 
 
+def case_hll(n=50_000_000):
+    import synth
+
+    zk, _ = synth.zipf_kv(n, seed=0)
+    return rel.key_hll(_cuda(zk))[1]
+
+
 CASES = {"distinct": case_distinct, "part": case_part, "stream": case_stream,
          "join": case_join, "lineitem": case_lineitem, "mlp": case_mlp, "batch": case_batch,
-         "shard": case_shard}
+         "shard": case_shard, "hll": case_hll}
 
 
 def main(argv) -> None:

@@ -31,6 +31,7 @@ OPS = {"sum": 0, "count": 1, "min": 2, "max": 3}
 VAR_AUTO, VAR_SMEM, VAR_GLOBAL, VAR_PARTITIONED = 0, 1, 2, 3
 PLAN_EXACT, PLAN_LEARNED, PLAN_GENERIC, PLAN_SKETCH = 1, 2, 4, 8
 PLAN_FELL_BACK = 0x10000
+PLAN_HLL_SIZED = 0x20000
 PLAN_TEST_STALL = 0x40000000  # test hook: the staged kernel's ring never drains
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 264, 64, 4, 21380
 
@@ -191,7 +192,7 @@ EXPORTS = ["rel_plan_size", "rel_groupby_agg", "rel_groupby_ws_bytes", "rel_join
            "rel_batch_ws_bytes", "rel_batch_prepare", "rel_batch_run", "rel_batch_results",
            "rel_batch_autotune", "rel_sketch_batched", "rel_sketch_batched_ws_bytes",
            "rel_plan_learned_rule", "rel_plan_size_batched", "rel_plan_size_batched_ws_bytes",
-           "rel_shard_ws_bytes", "rel_shard_split"]
+           "rel_shard_ws_bytes", "rel_shard_split", "rel_key_hll_ws_bytes", "rel_key_hll"]
 SHARD_MAX_WORLD = 64
 SKETCH_TOP, SKETCH_FEATURES = 32, 264
 STATIC_MAX_GROUPS = 32768
@@ -285,6 +286,11 @@ def load(build_if_stale: bool = True):
         L.rel_plan_size_batched.restype = i32
         L.rel_plan_size_batched.argtypes = [ctypes.POINTER(GroupByDesc), i32, u32, vp,
                                             ctypes.c_size_t, ctypes.POINTER(Plan), vp]
+        L.rel_key_hll_ws_bytes.restype = u64
+        L.rel_key_hll_ws_bytes.argtypes = []
+        L.rel_key_hll.restype = i32
+        L.rel_key_hll.argtypes = [vp, i32, i64, vp, ctypes.c_size_t, vp,
+                                  ctypes.POINTER(ctypes.c_double), vp]
         L.rel_shard_ws_bytes.restype = u64
         L.rel_shard_ws_bytes.argtypes = [i32]
         L.rel_shard_split.restype = i32
@@ -465,6 +471,19 @@ def groupby_auto(q: dict, flags: int = 0, capacity: int | None = None,
 
 def auto_ws_bytes(q: dict) -> int:
     return int(load().rel_groupby_auto_ws_bytes(ctypes.byref(_Desc(q).d)))
+
+
+def key_hll(keys: torch.Tensor, stream=None):
+    """rel_key_hll: (registers uint32[4096] as numpy, estimate) of a key column."""
+    L = load()
+    if keys.dtype not in (torch.int32, torch.int64) or not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA int32 / int64 tensor")
+    ws = _ws(L.rel_key_hll_ws_bytes(), keys.device)
+    regs = np.zeros(4096, dtype=np.uint32)
+    est = ctypes.c_double()
+    _check(L.rel_key_hll(keys.data_ptr(), _DT[keys.dtype], keys.numel(), ws.data_ptr(), ws.numel(),
+                         regs.ctypes.data, ctypes.byref(est), _stream(stream)))
+    return regs, est.value
 
 
 def shard_split(keys: torch.Tensor, words: list, world: int, stream=None):

@@ -223,11 +223,12 @@ def test_learned_plan_needs_a_network_and_scratch(L):
     d, keep = _desc(100)
     plan = rel.Plan()
     assert L.rel_planner_set(None, None) == rel.REL_OK
-    # without workspace: the scratch size comes back (sketch + 2 KB) before any GPU work
+    # without workspace: the scratch size comes back (sketch + 2 KB of features and
+    # outputs + 16 KB of HyperLogLog registers) before any GPU work
     r = L.rel_plan_size(rel.OP_GROUPBY, ctypes.byref(d), rel.PLAN_LEARNED, 0, None, 0,
                         ctypes.byref(plan), None)
     assert r == rel.REL_E_CAPACITY
-    assert plan.scratch_bytes == L.rel_sketch_ws_bytes() + 2048
+    assert plan.scratch_bytes == L.rel_sketch_ws_bytes() + 2048 + 4 * 4096
 
 
 def test_forced_partitioned_needs_key_value_shape(L):

@@ -82,3 +82,8 @@ def test_learned_plan_every_group(big):
     planner.use_default()
     keys, aggs, plan = rel.groupby_auto(q, flags=rel.PLAN_LEARNED | rel.PLAN_SKETCH)
     _assert_every_group(canon_groupby(keys, aggs), ek, ea)
+    # the Zipf sample sees most keys once: the full-data HyperLogLog sizes the
+    # plan and no exact re-plan is needed
+    assert not (plan.flags & rel.PLAN_FELL_BACK), plan
+    if kind == "zipf":
+        assert plan.flags & rel.PLAN_HLL_SIZED

@@ -2,6 +2,8 @@
 integer fields bit-exact, features to float32 rounding -- and of group-bys
 planned from it (hot keys pinned in thread-private slots) against the oracle
 group-by."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -10,7 +12,7 @@ import oracle
 import synth
 from paper_2608_13696_gb300 import rel
 
-from gpu_util import canon_groupby, query_to_cuda
+from gpu_util import canon_groupby, cuda, query_to_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -105,3 +107,44 @@ def test_sketch_batched_matches_oracle():
         assert bytes(s.hll) == e["hll"].tobytes()
         single = rel.sketch(query_to_cuda(CASES[n]))
         assert bytes(single.features) == bytes(s.features)
+
+
+@pytest.mark.parametrize("key_type", ["int64", "int32"])
+@pytest.mark.parametrize("n,offset", [(1, 0), (4097, 1), (1_000_003, 0), (3_000_001, 3)])
+def test_key_hll_registers_match_oracle(key_type, n, offset):
+    """The full-data HyperLogLog: registers bit for bit as the oracle's, over
+    ragged sizes and unaligned columns (scalar loads)."""
+    dt = np.int64 if key_type == "int64" else np.int32
+    lo, hi = (-(2**62), 2**62) if key_type == "int64" else (-(2**31), 2**31 - 1)
+    k = synth.uniform(n + offset, lo, hi, seed=n, tag=7, dtype=dt)
+    regs, est = rel.key_hll(cuda(k)[offset:])
+    eregs, eest = oracle.key_hll(k[offset:])
+    np.testing.assert_array_equal(regs, eregs)
+    assert abs(est - eest) <= 1e-9 * max(1.0, eest)
+
+
+def test_learned_plan_sizes_long_tails_by_hyperloglog():
+    """A large input whose sample saw its keys once: the learned plan sizes
+    from the full-data HyperLogLog (within its error, 25 % headroom) instead
+    of the network's guess, and the group-by is exact."""
+    from paper_2608_13696_gb300 import planner
+
+    if not os.path.exists(planner.DEFAULT_WEIGHTS):
+        pytest.skip("no trained network")
+    planner.use_default()
+    # 6e6 rows over 3e6 key values: ~2.6e6 groups, a sample of singletons
+    k = synth.uniform(6_000_000, 0, 3_000_000, seed=71, tag=1)
+    v = synth.uniform(6_000_000, -9, 9, seed=71, tag=2)
+    qc = {"cols": [cuda(k), cuda(v)], "keys": [0], "preds": [],
+          "aggs": [("sum", 1, []), ("count", 1, [])]}
+    plan = rel.plan_groupby(qc, flags=rel.PLAN_LEARNED | rel.PLAN_SKETCH)
+    true = np.unique(k).size
+    assert plan.flags & rel.PLAN_HLL_SIZED
+    lo, hi = 1.25 * true * (1 - 0.05), 1.25 * true * (1 + 0.05) + 1
+    assert min(lo, len(k)) <= plan.est_groups <= min(hi, len(k))  # never above the rows
+    keys, aggs, p2 = rel.groupby_auto(qc, flags=rel.PLAN_LEARNED | rel.PLAN_SKETCH)
+    assert not (p2.flags & rel.PLAN_FELL_BACK)
+    ek, ea = oracle.groupby(oracle.kv_query(k, v, ops=("sum", "count")))
+    gk, ga = canon_groupby(keys, aggs)
+    np.testing.assert_array_equal(gk, ek)
+    np.testing.assert_array_equal(ga, ea)
