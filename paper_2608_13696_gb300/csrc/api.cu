@@ -421,7 +421,7 @@ uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 // Workspace after the header and spill table: histogram, partition starts,
 // records.
 struct PartLayout {
-  uint64_t hist, starts, recs, end;
+  uint64_t hist, starts, cursor, hot, recs, end;
 };
 
 PartLayout part_layout(int64_t slots, int32_t n_aggs, int bits, int64_t n_rows) {
@@ -429,7 +429,9 @@ PartLayout part_layout(int64_t slots, int32_t n_aggs, int bits, int64_t n_rows) 
   const uint64_t P = 1ull << bits;
   L.hist = align_up(gb_ws_bytes(slots, n_aggs), 256);
   L.starts = align_up(L.hist + 4ull * P * PART_MAX_GRID, 256);
-  L.recs = align_up(L.starts + 8ull * (P + 1), 256);
+  L.cursor = align_up(L.starts + 8ull * (P + 1), 256);
+  L.hot = align_up(L.cursor + 4ull * P, 256);
+  L.recs = align_up(L.hot + 4ull * ((P + 31) / 32), 256);
   L.end = L.recs + sizeof(PartRec) * (uint64_t)(n_rows > 0 ? n_rows : 1);
   return L;
 }
@@ -450,6 +452,8 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   p.part_bits = (uint32_t)plan->part_bits;
   p.hist = (uint32_t*)(base + L.hist);
   p.part_start = (unsigned long long*)(base + L.starts);
+  p.cursor = (unsigned int*)(base + L.cursor);
+  p.hot = (uint32_t*)(base + L.hot);
   p.recs = (PartRec*)(base + L.recs);
   uint32_t grid = 2u * (uint32_t)relhost::device_sms();
   p.fixed_grid = grid > PART_MAX_GRID ? PART_MAX_GRID : grid;

@@ -916,9 +916,17 @@ __global__ void __launch_bounds__(1024) gb_part_scan2(const __grid_constant__ Gb
   unsigned long long s = 0;
   for (uint32_t i = b; i < e; ++i) s += p.part_start[i];
   unsigned long long run = block_exclusive_scan(s, &total);
+  // a partition far above the average is "hot": its records are placed by
+  // per-CTA cursors (dense runs per CTA); the others share one cursor each
+  // (few records apiece, so their sectors fill from many CTAs within L2)
+  for (uint32_t w = threadIdx.x; w < (P + 31) / 32; w += blockDim.x) p.hot[w] = 0;
+  __syncthreads();
+  const unsigned long long hot_min = 4 * (total / P) + 4096;
   for (uint32_t i = b; i < e; ++i) {
     const unsigned long long v = p.part_start[i];
     p.part_start[i] = run;
+    p.cursor[i] = (unsigned int)run;
+    if (v > hot_min) atomicOr(&p.hot[i >> 5], 1u << (i & 31));
     run += v;
   }
   if (threadIdx.x == 0) p.part_start[P] = total;

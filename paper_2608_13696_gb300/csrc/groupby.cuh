@@ -91,6 +91,8 @@ struct GbParams {
   uint32_t* hist;           // [P][fixed_grid] counts, then exclusive offsets
   unsigned long long* part_start;  // [P + 1] first record of each partition
   PartRec* recs;            // records of every non-pinned row
+  unsigned int* cursor;     // [P] next free record of each partition (shared by all CTAs)
+  uint32_t* hot;            // [P / 32] bit p: partition p is large (per-CTA cursors)
   // global table (or key set in MODE_KEYSET)
   uint64_t* tkeys;
   unsigned long long* taggs;  // slots x n_aggs words

@@ -326,7 +326,12 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
   for (uint32_t i = tid; i < P; i += SP_BLOCK)
     ctr[i] = SCATTER ? (unsigned int)(p.part_start[i] + p.hist[(size_t)i * p.fixed_grid + blockIdx.x])
                      : 0u;
+  uint32_t* hotb = (uint32_t*)(ctr + P);  // [P / 32] copy of the hot-partition bits
+  if (SCATTER)
+    for (uint32_t i = tid; i < (P + 31) / 32; i += SP_BLOCK) hotb[i] = p.hot[i];
   const unsigned long long total = SCATTER ? p.part_start[P] : 0;
+  const int lane = tid & 31;
+  const unsigned lanes_below = (1u << lane) - 1u;
   __syncthreads();
 
   const KT* keys = (const KT*)p.col[p.key_col[0]];
@@ -374,46 +379,64 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
     if (base + step < n) load(base + step, nek, nval, nok);
 #pragma unroll
     for (int j = 0; j < ST_U; ++j) {
-      if (!(okm >> j & 1)) continue;
-      if (PIN) {
-        const uint32_t s = small_slot_of(ek[j], tmask, p.tiny_mult);
-        if (pk[s] == ek[j] && ek[j] != 0) {
+      // rec: the row becomes a record of partition part (not pinned, not INT64_MIN)
+      bool rec = false;
+      uint32_t part = 0;
+      if (okm >> j & 1) {
+        bool pinned = false;
+        if (PIN) {
+          const uint32_t s = small_slot_of(ek[j], tmask, p.tiny_mult);
+          if (pk[s] == ek[j] && ek[j] != 0) {
+            pinned = true;
+            if (SCATTER) {
+              uint64_t w[NA];
+              words_of<NA>(val[j], w);
+              uint64_t* t = acc + (size_t)dense[s] * NA * SP_BLOCK + tid;
+#pragma unroll
+              for (int a = 0; a < NA; ++a) {
+                const uint64_t o = t[a * SP_BLOCK];
+                t[a * SP_BLOCK] = umax_word<NA>(a) ? (o > w[a] ? o : w[a]) : o + w[a];
+              }
+            }
+          }
+        }
+        if (!pinned && ek[j] == 0) {
           if (SCATTER) {
             uint64_t w[NA];
             words_of<NA>(val[j], w);
-            uint64_t* t = acc + (size_t)dense[s] * NA * SP_BLOCK + tid;
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-              const uint64_t o = t[a * SP_BLOCK];
-              t[a * SP_BLOCK] = umax_word<NA>(a) ? (o > w[a] ? o : w[a]) : o + w[a];
-            }
+            atomicAdd(&p.hdr->n_side, 1ull);
+            red_global<NA>(p.hdr->side_aggs, w);
           }
-          continue;
+        } else if (!pinned) {
+          rec = true;
+          part = part_of(ek[j], p.part_bits);
         }
       }
-      if (ek[j] == 0) {
-        if (SCATTER) {
-          uint64_t w[NA];
-          words_of<NA>(val[j], w);
-          atomicAdd(&p.hdr->n_side, 1ull);
-          red_global<NA>(p.hdr->side_aggs, w);
-        }
+      if (!SCATTER) {
+        if (rec) atomicAdd(&ctr[part], 1u);
         continue;
       }
-      const uint32_t part = part_of(ek[j], p.part_bits);
-      if (!SCATTER) {
-        atomicAdd(&ctr[part], 1u);
-      } else {
-        const unsigned long long pos = atomicAdd(&ctr[part], 1u);
-        if (pos >= total) {  // the passes disagreed: report, never write past the buffer
-          atomicOr(&p.hdr->timeout, 2u);
-          continue;
-        }
-        PartRec r;
-        r.ek = ek[j];
-        r.val = (long long)val[j];
-        p.recs[pos] = r;
+      // hot partitions: this CTA's own cursor; the others: the partition's
+      // shared cursor, one atomic per partition present in the warp
+      const bool hot = rec && (hotb[part >> 5] >> (part & 31) & 1u);
+      unsigned long long pos = 0;
+      if (hot) pos = atomicAdd(&ctr[part], 1u);
+      const bool cold = rec && !hot;
+      const unsigned grp = __match_any_sync(0xffffffffu, cold ? part : (0x80000000u | (unsigned)lane));
+      const int leader = __ffs(grp) - 1;
+      unsigned int cb = 0;
+      if (cold && lane == leader) cb = atomicAdd(p.cursor + part, (unsigned int)__popc(grp));
+      cb = __shfl_sync(0xffffffffu, cb, leader);
+      if (cold) pos = (unsigned long long)cb + __popc(grp & lanes_below);
+      if (!rec) continue;
+      if (pos >= total) {  // the passes disagreed: report, never write past the buffer
+        atomicOr(&p.hdr->timeout, 2u);
+        continue;
       }
+      PartRec r;
+      r.ek = ek[j];
+      r.val = (long long)val[j];
+      p.recs[pos] = r;
     }
 #pragma unroll
     for (int j = 0; j < ST_U; ++j) {
@@ -428,7 +451,6 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
     return;
   }
   if (PIN) {
-    const int lane = tid & 31;
     for (int d = 0; d < PM; ++d) {
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
@@ -459,7 +481,7 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
 size_t ppass_smem(int na, bool pin, bool scatter, uint32_t part_bits) {
   size_t b = 416 + 8 * ST_PIN_LIMIT * 4;
   if (pin && scatter) b += (size_t)8 * (na == 4 ? pin_max<4>() : pin_max<2>()) * na * SP_BLOCK;
-  return b + 4ull * (1u << part_bits);
+  return b + 4ull * (1u << part_bits) + (scatter ? 4ull * (((1u << part_bits) + 31) / 32) : 0);
 }
 
 template <class KT, int NA, bool PIN, bool SCATTER>
