@@ -17,6 +17,9 @@
  *    owned by the caller; the library never allocates device or pinned
  *    memory.  Descriptors, plans, rel_join_table and *_host pointers are HOST
  *    memory owned by the caller.
+ *  - A workspace (ws) starts on a 256-byte boundary, as every cudaMalloc and
+ *    PyTorch allocation does; any other address is REL_E_INVALID before any
+ *    device work (the tables in it are read with 32-byte vector loads).
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *    stream).  A call that writes a *_host count synchronises that stream
  *    before returning; with a NULL *_host pointer the call does not block.

@@ -1148,6 +1148,8 @@ rel_status rel_mlp_backward(const void* bf16_params, const float* x, const float
                             const float* out, const float* t_ndv, const int32_t* t_var,
                             int32_t batch, void* ws, size_t ws_bytes, float* grad, float* loss,
                             void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("mlp: workspace not 256-byte aligned"), REL_E_INVALID;
   if (batch < 0) return set_error("mlp: batch < 0"), REL_E_INVALID;
   if (!grad || !loss || (batch > 0 && (!bf16_params || !x || !acts || !out || !t_ndv || !t_var)))
     return set_error("mlp: NULL argument"), REL_E_INVALID;
@@ -1211,6 +1213,8 @@ uint64_t rel_groupby_auto_ws_bytes(const rel_groupby_desc* d) {
 rel_status rel_groupby_auto(const rel_groupby_desc* d, uint32_t flags, void* ws, size_t ws_bytes,
                             int64_t* out_keys, int64_t* const* out_aggs, int64_t out_capacity,
                             int64_t* n_groups_host, rel_plan* plan_out, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("group-by: workspace not 256-byte aligned"), REL_E_INVALID;
   rel_status r = validate_desc(d);
   if (r) return r;
   const uint64_t need = rel_groupby_auto_ws_bytes(d);
@@ -1236,6 +1240,8 @@ rel_status rel_groupby_auto(const rel_groupby_desc* d, uint32_t flags, void* ws,
 
 rel_status rel_sketch(const rel_groupby_desc* d, void* ws, size_t ws_bytes, rel_sketch_info* out,
                       void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("sketch: workspace not 256-byte aligned"), REL_E_INVALID;
   rel_status r = validate_desc(d);
   if (r) return r;
   if (!out) return set_error("sketch: NULL output"), REL_E_INVALID;
@@ -1264,6 +1270,8 @@ uint64_t rel_sketch_batched_ws_bytes(int32_t n) {
 
 rel_status rel_sketch_batched(const rel_groupby_desc* descs, int32_t n, void* ws, size_t ws_bytes,
                               rel_sketch_info* out, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("sketch: workspace not 256-byte aligned"), REL_E_INVALID;
   if (n < 0 || (n > 0 && (!descs || !out)))
     return set_error("sketch: bad arguments"), REL_E_INVALID;
   if (n == 0) return REL_OK;
@@ -1312,6 +1320,8 @@ uint64_t rel_plan_size_batched_ws_bytes(int32_t n) {
 
 rel_status rel_plan_size_batched(const rel_groupby_desc* descs, int32_t n, uint32_t flags,
                                  void* ws, size_t ws_bytes, rel_plan* plans, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("plan: workspace not 256-byte aligned"), REL_E_INVALID;
   if (n < 0 || (n > 0 && (!descs || !plans)))
     return set_error("plan: bad batched arguments"), REL_E_INVALID;
   if (!(flags & REL_PLAN_LEARNED) || (flags & (REL_PLAN_EXACT | REL_PLAN_GENERIC | REL_PLAN_FORCE_MASK)))
@@ -1366,6 +1376,8 @@ uint64_t rel_key_hll_ws_bytes(void) { return 4ull * HLL_REGS; }
 
 rel_status rel_key_hll(const void* keys, int32_t key_type, int64_t n, void* ws, size_t ws_bytes,
                        uint32_t* regs_host, double* estimate, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("hll: workspace not 256-byte aligned"), REL_E_INVALID;
   if (n < 0 || (n > 0 && !keys) || !regs_host || !estimate)
     return set_error("hll: bad arguments"), REL_E_INVALID;
   if (key_type != REL_I32 && key_type != REL_I64)
@@ -1394,6 +1406,8 @@ uint64_t rel_join_ws_bytes(int64_t n_build) {
 
 rel_status rel_plan_size(int32_t op, const void* desc, uint32_t flags, int64_t groups_hint,
                          void* ws, size_t ws_bytes, rel_plan* plan, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("plan: workspace not 256-byte aligned"), REL_E_INVALID;
   if (!plan) return set_error("plan: NULL plan"), REL_E_INVALID;
   if (op == REL_OP_GROUPBY)
     return plan_groupby((const rel_groupby_desc*)desc, flags, groups_hint, ws, ws_bytes, plan,
@@ -1414,6 +1428,8 @@ rel_status rel_plan_size(int32_t op, const void* desc, uint32_t flags, int64_t g
 rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void* ws,
                            size_t ws_bytes, int64_t* out_keys, int64_t* const* out_aggs,
                            int64_t out_capacity, int64_t* n_groups_host, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("group-by: workspace not 256-byte aligned"), REL_E_INVALID;
   rel_status r = validate_desc(d);
   if (r) return r;
   if (!plan) return set_error("group-by: NULL plan"), REL_E_INVALID;
@@ -1517,6 +1533,8 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
 
 rel_status rel_join_build(const int64_t* keys, const int64_t* payload, int64_t n_build, void* ws,
                           size_t ws_bytes, rel_join_table* table, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("join: workspace not 256-byte aligned"), REL_E_INVALID;
   if (!table) return set_error("join: NULL table handle"), REL_E_INVALID;
   if (n_build < 0 || n_build > MAX_INDEX_ROWS)
     return set_error("join: n_build outside [0, 2^31-1]"), REL_E_UNSUPPORTED;

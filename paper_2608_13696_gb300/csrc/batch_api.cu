@@ -304,6 +304,8 @@ uint64_t rel_batch_ws_bytes(const rel_batch_groupby* gb, int32_t n_gb, const rel
 rel_status rel_batch_prepare(const rel_batch_groupby* gb, int32_t n_gb, const rel_batch_join* jn,
                              int32_t n_jn, const rel_batch_config* cfg, void* ws, size_t ws_bytes,
                              rel_batch_handle* handle, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("batch: workspace not 256-byte aligned"), REL_E_INVALID;
   if (!handle) return set_error("batch: NULL handle"), REL_E_INVALID;
   return prepare(gb, n_gb, jn, n_jn, cfg, ws, ws_bytes, (HandleImpl*)handle, (cudaStream_t)stream);
 }
@@ -358,6 +360,8 @@ rel_status rel_batch_autotune(const rel_batch_groupby* gb, int32_t n_gb, const r
                               int32_t n_jn, const rel_batch_config* cands, int32_t n_cands,
                               int32_t reps, void* ws, size_t ws_bytes, rel_batch_handle* handle,
                               rel_batch_config* best, float* ms, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return set_error("batch: workspace not 256-byte aligned"), REL_E_INVALID;
   if (!cands || n_cands < 1 || reps < 1 || !handle || !best)
     return set_error("batch: bad autotune arguments"), REL_E_INVALID;
   rel_status r = validate(gb, n_gb, jn, n_jn);

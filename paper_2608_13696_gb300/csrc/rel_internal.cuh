@@ -205,6 +205,9 @@ constexpr uint64_t TEST_WAIT_LIMIT_NS = 20000000ull;  // 20 ms
 
 namespace relhost {
 void set_error(const char* fmt, ...);
+// A workspace must start on a 256-byte boundary (every cudaMalloc and
+// PyTorch allocation does): tables in it are read with 32-byte vector loads.
+inline bool ws_unaligned(const void* ws) { return ws && ((uintptr_t)ws & 255u) != 0; }
 rel_status cuda_fail(cudaError_t e, const char* what);
 void count_launch(unsigned n = 1);
 int device_sms();

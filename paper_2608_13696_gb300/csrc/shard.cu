@@ -106,6 +106,8 @@ uint64_t rel_shard_ws_bytes(int32_t world) {
 rel_status rel_shard_split(const int64_t* keys, const int64_t* const* words, int32_t n_words,
                            int64_t n, int32_t world, int64_t* out_keys, int64_t* const* out_words,
                            int64_t* counts_host, void* ws, size_t ws_bytes, void* stream) {
+  if (relhost::ws_unaligned(ws))
+    return relhost::set_error("shard: workspace not 256-byte aligned"), REL_E_INVALID;
   using namespace rel;
   if (world < 1 || world > REL_SHARD_MAX_WORLD)
     return relhost::set_error("shard: world must be 1..%d", REL_SHARD_MAX_WORLD), REL_E_UNSUPPORTED;

@@ -18,7 +18,9 @@ CASE (inputs seeded and synthetic, as in the bench):
   shard     owner split of 2e6 partial groups over 8 ranks
   hll       full-data HyperLogLog of 5e7 Zipf(1.1) keys
 Sizes keep every case below a few GB of device memory, with inputs above the
-129 MB L2 where the kernel streams.
+129 MB L2 where the kernel streams.  Algorithmic bytes: inputs read once and
+outputs written once (16-byte records for the partition passes, 16 bytes
+per match for the join probe); hash-table and workspace traffic excluded.
 """
 from __future__ import annotations
 
@@ -43,7 +45,8 @@ def case_distinct(n=50_000_000):
 
     zk, zv = synth.zipf_kv(n, seed=0)
     q = kv_query(_cuda(zk), _cuda(zv), ops=("count",))
-    return rel.plan_groupby(q, flags=rel.PLAN_EXACT).est_groups
+    rel.plan_groupby(q, flags=rel.PLAN_EXACT)
+    return {"gb_main_keyset": (n, "rows", 8 * n)}
 
 
 def case_part(n=50_000_000):
@@ -53,8 +56,15 @@ def case_part(n=50_000_000):
     q = kv_query(_cuda(zk), _cuda(zv))
     p = rel.plan_groupby(q, flags=rel.plan_force(rel.VAR_PARTITIONED) | rel.PLAN_SKETCH,
                          groups_hint=3_300_000)
-    k, _ = rel.groupby(q, plan=p, capacity=4_000_000)
-    return k.numel()
+    k, aggs = rel.groupby(q, plan=p, capacity=4_000_000)
+    kd = q["cols"][0]
+    hot = torch.tensor([p.hot_keys[i] for i in range(p.n_hot)] + [-(1 << 63)], dtype=torch.int64,
+                       device=kd.device)
+    recs = int(n - torch.isin(kd, hot).sum().item())  # rows written as partition records
+    out = k.numel() * 8 * (1 + len(aggs))
+    return {"gb_part_hist": (n, "rows", 8 * n), "gb_part_scatter": (n, "rows", 16 * n + 16 * recs),
+            "gb_part_scan": (n, "rows", None), "gb_part_agg": (n, "rows", 16 * recs + out),
+            "gb_compact": (n, "rows", out), "records": recs, "groups": k.numel()}
 
 
 def case_stream(n=50_000_000):
@@ -63,8 +73,8 @@ def case_stream(n=50_000_000):
     fk, fv = synth.few_keys_kv(n, n_keys=4, seed=0)
     q = kv_query(_cuda(fk), _cuda(fv))
     p = rel.plan_groupby(q, flags=rel.PLAN_SKETCH, groups_hint=4)
-    k, _ = rel.groupby(q, plan=p, capacity=8)
-    return k.numel()
+    rel.groupby(q, plan=p, capacity=8)
+    return {"gb_stream": (n, "rows", 16 * n)}
 
 
 def case_join(nb=1_000_000, np_=16_000_000):
@@ -73,7 +83,9 @@ def case_join(nb=1_000_000, np_=16_000_000):
     bk, bp = synth.join_build(nb, seed=0)
     pk, _ = synth.join_probe(np_, nb, seed=0)
     t = rel.JoinTable(_cuda(bk), _cuda(bp))
-    return t.probe(_cuda(pk), capacity=np_)[0].numel()
+    m = t.probe(_cuda(pk), capacity=np_)[0].numel()
+    return {"join_build": (nb, "build rows", 16 * nb), "join_probe": (np_, "probes", 8 * np_ + 16 * m),
+            "matches": m}
 
 
 def case_lineitem(n=20_000_000):
@@ -84,8 +96,11 @@ def case_lineitem(n=20_000_000):
     q = lineitem_query(synth.lineitem(n, seed=0))
     q["cols"] = [_cuda(c) for c in q["cols"]]
     p = rel.plan_groupby(q, flags=rel.PLAN_EXACT | rel.PLAN_SKETCH)
-    k, _ = rel.groupby(q, plan=p)
-    return k.numel()
+    rel.groupby(q, plan=p)
+    used = set(q["keys"]) | {c[0] for c in q.get("preds", [])}
+    return {"gb_main_staged_keyset": (n, "rows", sum(q["cols"][c].nbytes for c in used)),
+            "gb_main_regs": (n, "rows", sum(c.nbytes for c in q["cols"])),
+            "sketch": (1, "sketch", None)}
 
 
 def case_mlp(batch=256):
@@ -103,7 +118,8 @@ def case_mlp(batch=256):
     rel.mlp_backward(bf, x, acts, y, t, v, grad, loss)
     m, s = torch.zeros_like(p), torch.zeros_like(p)
     rel.mlp_adamw(p, bf, m, s, grad, 1)
-    return float(loss.item())
+    return {"mlp_forward": (batch, "samples", None), "mlp_backward": (batch, "samples", None),
+            "mlp_adamw": (rel.MLP_PARAMS, "parameters", None), "loss": float(loss.item())}
 
 
 def case_batch():
@@ -122,23 +138,29 @@ def case_batch():
               rel.VAR_SMEM if e <= 512 else rel.VAR_GLOBAL) for e in est]
     b = batched.make_batch(gb, jn, sizes).prepare((512, 4, 1, 512))
     b.run()
-    counts, _ = b.results()
-    return sum(counts)
+    b.results()
+    rows = sum(k.numel() for k, _ in gb)
+    gb_bytes = sum(k.nbytes + v.nbytes for k, v in gb)
+    probes = sum(x[2].numel() for x in jn)
+    jn_bytes = sum(sum(t.nbytes for t in x) for x in jn)
+    return {"batch_a": (rows + probes, "rows", gb_bytes + jn_bytes),
+            "batch_b": (rows + probes, "rows", None)}
 
 
 def case_shard(n=2_000_000, world=8):
     g = torch.Generator().manual_seed(0)
     k = torch.randint(-(1 << 62), 1 << 62, (n,), generator=g).cuda()
     w = [torch.randint(-1000, 1000, (n,), generator=g).cuda() for _ in range(4)]
-    _, _, counts = rel.shard_split(k, w, world)
-    return counts
+    rel.shard_split(k, w, world)
+    return {"shard_scatter": (n, "groups", 2 * 8 * 5 * n)}
 
 
 def case_hll(n=50_000_000):
     import synth
 
     zk, _ = synth.zipf_kv(n, seed=0)
-    return rel.key_hll(_cuda(zk))[1]
+    rel.key_hll(_cuda(zk))
+    return {"hll": (n, "rows", 8 * n)}
 
 
 CASES = {"distinct": case_distinct, "part": case_part, "stream": case_stream,
@@ -147,11 +169,16 @@ CASES = {"distinct": case_distinct, "part": case_part, "stream": case_stream,
 
 
 def main(argv) -> None:
+    """Runs the named cases; prints per case one line `NAME ok JSON`, the
+    JSON mapping each kernel id to [units, unit name, algorithmic bytes or
+    null] for the summary of its capture."""
+    import json
+
     rel.load()
     for name in argv or list(CASES):
         out = CASES[name]()
         torch.cuda.synchronize()
-        print(name, "ok", out)
+        print(name, "ok", json.dumps(out))
 
 
 if __name__ == "__main__":

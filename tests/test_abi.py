@@ -120,20 +120,24 @@ def test_groupby_agg_argument_checks(L):
     plan = rel.Plan()
     plan.slots = 24  # not a power of two
     n = ctypes.c_int64()
-    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x100, 1 << 20, 0x10, None, 0,
                              ctypes.byref(n), None) == rel.REL_E_INVALID
     plan.slots = 1024
     plan.smem_slots = 24
-    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x100, 1 << 20, 0x10, None, 0,
                              ctypes.byref(n), None) == rel.REL_E_INVALID
     plan.smem_slots = 0
     plan.tiny_slots = 12
-    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 1 << 20, 0x10, None, 0,
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x100, 1 << 20, 0x10, None, 0,
                              ctypes.byref(n), None) == rel.REL_E_INVALID
     plan.tiny_slots = 0
     # workspace too small: capacity error before any device work
-    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x10, 100, 0x10, None, 0,
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x100, 100, 0x10, None, 0,
                              ctypes.byref(n), None) == rel.REL_E_CAPACITY
+    # a workspace off a 256-byte boundary is rejected before any device work
+    assert L.rel_groupby_agg(ctypes.byref(d), ctypes.byref(plan), 0x110, 1 << 20, 0x10, None, 0,
+                             ctypes.byref(n), None) == rel.REL_E_INVALID
+    assert b"aligned" in L.rel_last_error()
 
 
 def test_static_groupby_checks_before_any_device_work(L):
@@ -197,7 +201,8 @@ def test_join_argument_checks(L):
     assert L.rel_join_build(None, None, -1, None, 0, ctypes.byref(t), None) == rel.REL_E_UNSUPPORTED
     assert L.rel_join_build(None, None, 1 << 31, None, 0, ctypes.byref(t), None) == rel.REL_E_UNSUPPORTED
     assert L.rel_join_build(None, None, 10, None, 0, ctypes.byref(t), None) == rel.REL_E_INVALID
-    assert L.rel_join_build(0x10, 0x10, 10, 0x10, 10, ctypes.byref(t), None) == rel.REL_E_CAPACITY
+    assert L.rel_join_build(0x10, 0x10, 10, 0x100, 10, ctypes.byref(t), None) == rel.REL_E_CAPACITY
+    assert L.rel_join_build(0x10, 0x10, 10, 0x108, 1 << 20, ctypes.byref(t), None) == rel.REL_E_INVALID
     n = ctypes.c_int64()
     # an unbuilt handle is rejected
     assert L.rel_join_probe(ctypes.byref(t), 0x10, 10, 0x10, 0x10, 0x10, 10, ctypes.byref(n),

@@ -2,6 +2,8 @@
 against the oracle: bit-exact pair sets after sorting by (probe_idx,
 build_idx), at small sizes with duplicate and INT64_MIN keys, and at the
 full 10^6 x 1.6*10^7 size the benchmark times."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -89,3 +91,27 @@ def test_unaligned_inputs():
     want = oracle.join(bk[1:], bp[1:], pk[1:])
     for g, w in zip(got, want):
         np.testing.assert_array_equal(g, w)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_unique_keys_small_tables(seed):
+    # 1..16 distinct keys in tables of 16 or 32 slots: clustered probe
+    # sequences that wrap past the table's end, hits and misses
+    rng = np.random.default_rng(100 + seed)
+    nb = int(rng.integers(1, 17))
+    bk = rng.choice(np.arange(-1000, 1000, dtype=np.int64), nb, replace=False)
+    bp = rng.integers(-(2**63), 2**63 - 1, nb, dtype=np.int64)
+    pk = np.concatenate([bk, rng.integers(-1200, 1200, 500).astype(np.int64)])
+    rng.shuffle(pk)
+    assert_same(bk, bp, pk)
+
+
+def test_unaligned_workspace_rejected():
+    L = rel.load()
+    bk = cuda(np.arange(100, dtype=np.int64))
+    n = L.rel_join_ws_bytes(100)
+    ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+    t = rel.JoinTableC()
+    st = L.rel_join_build(bk.data_ptr(), bk.data_ptr(), 100, ws.data_ptr() + 8, n, ctypes.byref(t), None)
+    assert st == rel.REL_E_INVALID
+    assert b"aligned" in L.rel_last_error()
