@@ -176,6 +176,8 @@ def algo_bytes(kernel, part, inp, res):
             return cols[part][0].nbytes
         if kernel == "gb_part_scatter":
             return sum(c.nbytes for c in cols[part]) + 16 * recs
+        if kernel == "gb_part_l2":  # level-1 records read, final records written
+            return 32 * recs
         if kernel == "gb_part_agg":
             k, aggs = res[part]
             return 16 * recs + k.numel() * 8 * (1 + len(aggs))

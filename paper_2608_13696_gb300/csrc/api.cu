@@ -421,18 +421,23 @@ uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 // Workspace after the header and spill table: histogram, partition starts,
 // records.
 struct PartLayout {
-  uint64_t hist, starts, cursor, hot, recs, end;
+  uint64_t hist, starts, cursor, cursor1, l2_tiles, recs, recs1, end;
 };
 
 PartLayout part_layout(int64_t slots, int32_t n_aggs, int bits, int64_t n_rows) {
   PartLayout L;
   const uint64_t P = 1ull << bits;
+  const uint64_t bins = 1ull << PART_L1_BITS;
   L.hist = align_up(gb_ws_bytes(slots, n_aggs), 256);
   L.starts = align_up(L.hist + 4ull * P * PART_MAX_GRID, 256);
   L.cursor = align_up(L.starts + 8ull * (P + 1), 256);
-  L.hot = align_up(L.cursor + 4ull * P, 256);
-  L.recs = align_up(L.hot + 4ull * ((P + 31) / 32), 256);
-  L.end = L.recs + sizeof(PartRec) * (uint64_t)(n_rows > 0 ? n_rows : 1);
+  L.cursor1 = align_up(L.cursor + 4ull * P, 256);
+  L.l2_tiles = align_up(L.cursor1 + 4ull * bins, 256);
+  L.recs = align_up(L.l2_tiles + 4ull * (bins + 1), 256);
+  const uint64_t rec_bytes = sizeof(PartRec) * (uint64_t)(n_rows > 0 ? n_rows : 1);
+  // level-1 records of the streaming scatter when there are two levels
+  L.recs1 = align_up(L.recs + rec_bytes, 256);
+  L.end = bits > PART_L1_BITS ? L.recs1 + rec_bytes : L.recs1;
   return L;
 }
 
@@ -453,8 +458,10 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   p.hist = (uint32_t*)(base + L.hist);
   p.part_start = (unsigned long long*)(base + L.starts);
   p.cursor = (unsigned int*)(base + L.cursor);
-  p.hot = (uint32_t*)(base + L.hot);
+  p.cursor1 = (unsigned int*)(base + L.cursor1);
+  p.l2_tiles = (unsigned int*)(base + L.l2_tiles);
   p.recs = (PartRec*)(base + L.recs);
+  p.recs1 = p.part_bits > PART_L1_BITS ? (PartRec*)(base + L.recs1) : nullptr;
   uint32_t grid = 2u * (uint32_t)relhost::device_sms();
   p.fixed_grid = grid > PART_MAX_GRID ? PART_MAX_GRID : grid;
   const uint32_t agg_slots = p.smem_slots;
@@ -465,13 +472,13 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   }
   rel_status r;
   if (!plan->tile_rows && gb_ppass_stream_eligible(p, shape, plan->n_hot)) {
-    // one CTA per SM: fewer (partition, CTA) write cursors, so the partly
-    // written record sectors stay in L2 until they fill
-    p.fixed_grid = (uint32_t)relhost::device_sms() < PART_MAX_GRID ? (uint32_t)relhost::device_sms()
-                                                                   : PART_MAX_GRID;
+    // the CTAs that fit on the SMs at once (the pinned keys' thread-private
+    // words fill most of their shared memory)
+    p.fixed_grid = gb_ppass_stream_grid() < PART_MAX_GRID ? gb_ppass_stream_grid() : PART_MAX_GRID;
     if ((r = gb_launch_ppass_stream(p, shape, false, st))) return r;
     if ((r = gb_launch_part_scan(p, st))) return r;
     if ((r = gb_launch_ppass_stream(p, shape, true, st))) return r;
+    if (p.part_bits > PART_L1_BITS && (r = gb_launch_part_l2(p, st))) return r;
     p.smem_slots = agg_slots;
     return gb_launch_part_agg(p, shape, o, st);
   }
@@ -1116,7 +1123,8 @@ const char* rel_kernel_name(int32_t id) {
   static const char* names[] = {"gb_main_layered", "gb_main_keyset", "gb_compact",
                                 "join_build", "join_probe", "join_count", "sketch", "gb_main_regs",
                                 "gb_part_hist", "gb_part_scan", "gb_part_scatter",
-                                "gb_part_agg", "mlp", "batch_a", "batch_b", "gb_stream", "hll"};
+                                "gb_part_agg", "mlp", "batch_a", "batch_b", "gb_stream", "hll",
+                                "gb_part_l2"};
   return (id >= 0 && id < relhost::K_COUNT_IDS) ? names[id] : "?";
 }
 

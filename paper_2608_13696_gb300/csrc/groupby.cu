@@ -908,28 +908,36 @@ __global__ void __launch_bounds__(1024) gb_part_scan1(const __grid_constant__ Gb
 }
 
 // partition totals -> first record of each partition; part_start[P] = all.
+// Also the cursors of both scatter levels and the level-2 pass's tiles.
 __global__ void __launch_bounds__(1024) gb_part_scan2(const __grid_constant__ GbParams p) {
-  __shared__ unsigned long long total;
+  __shared__ unsigned long long total, tiles_total;
   const uint32_t P = 1u << p.part_bits;
   const uint32_t per = (P + blockDim.x - 1) / blockDim.x;
   const uint32_t b = threadIdx.x * per, e = b + per < P ? b + per : P;
   unsigned long long s = 0;
   for (uint32_t i = b; i < e; ++i) s += p.part_start[i];
   unsigned long long run = block_exclusive_scan(s, &total);
-  // a partition far above the average is "hot": its records are placed by
-  // per-CTA cursors (dense runs per CTA); the others share one cursor each
-  // (few records apiece, so their sectors fill from many CTAs within L2)
-  for (uint32_t w = threadIdx.x; w < (P + 31) / 32; w += blockDim.x) p.hot[w] = 0;
-  __syncthreads();
-  const unsigned long long hot_min = 4 * (total / P) + 4096;
   for (uint32_t i = b; i < e; ++i) {
     const unsigned long long v = p.part_start[i];
     p.part_start[i] = run;
     p.cursor[i] = (unsigned int)run;
-    if (v > hot_min) atomicOr(&p.hot[i >> 5], 1u << (i & 31));
     run += v;
   }
   if (threadIdx.x == 0) p.part_start[P] = total;
+  __syncthreads();
+  // level-1 bins: 2^shift1 consecutive partitions each
+  const uint32_t shift1 = p.part_bits > PART_L1_BITS ? p.part_bits - PART_L1_BITS : 0;
+  const uint32_t B1 = P >> shift1;
+  unsigned long long tiles = 0;
+  if (threadIdx.x < B1) {
+    const unsigned long long s1 = p.part_start[threadIdx.x << shift1];
+    const unsigned long long e1 = p.part_start[(threadIdx.x + 1) << shift1];
+    p.cursor1[threadIdx.x] = (unsigned int)s1;
+    tiles = (e1 - s1 + PART_TILE - 1) / PART_TILE;
+  }
+  const unsigned long long tp = block_exclusive_scan(tiles, &tiles_total);
+  if (threadIdx.x < B1) p.l2_tiles[threadIdx.x] = (unsigned int)tp;
+  if (threadIdx.x == 0) p.l2_tiles[B1] = (unsigned int)tiles_total;
 }
 
 // Insert-or-accumulate into a partition's shared-memory table; a key that

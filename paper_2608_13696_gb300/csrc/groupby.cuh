@@ -31,6 +31,13 @@ struct alignas(16) PartRec {
 };
 constexpr int PART_MAX_BITS = 14;  // at most 16384 partitions
 constexpr int PART_CHUNKS = 16;    // CTAs that may share one oversized partition
+// Streaming scatter in two levels: the first writes records into at most
+// 2^PART_L1_BITS bins (the top bits of the partition index), the second
+// splits every bin into its partitions.  Both sort a tile of PART_TILE
+// records by destination in shared memory and write each destination's run
+// contiguously.
+constexpr int PART_L1_BITS = 8;
+constexpr int PART_TILE = 4096;
 
 // Row shapes.  The specialised ones fix column types and aggregate kinds at
 // compile time; KV4 / KV2 hold their aggregates in the internal order
@@ -90,9 +97,11 @@ struct GbParams {
   uint32_t fixed_grid;      // CTAs of the histogram and scatter passes (equal)
   uint32_t* hist;           // [P][fixed_grid] counts, then exclusive offsets
   unsigned long long* part_start;  // [P + 1] first record of each partition
-  PartRec* recs;            // records of every non-pinned row
-  unsigned int* cursor;     // [P] next free record of each partition (shared by all CTAs)
-  uint32_t* hot;            // [P / 32] bit p: partition p is large (per-CTA cursors)
+  PartRec* recs;            // records of every non-pinned row, by partition
+  PartRec* recs1;           // streaming, part_bits > PART_L1_BITS: records by level-1 bin
+  unsigned int* cursor;     // [P] next free record of each partition
+  unsigned int* cursor1;    // [2^PART_L1_BITS] next free record of each level-1 bin
+  unsigned int* l2_tiles;   // [bins + 1] exclusive prefix of the level-2 tiles per bin
   // global table (or key set in MODE_KEYSET)
   uint64_t* tkeys;
   unsigned long long* taggs;  // slots x n_aggs words
@@ -123,7 +132,11 @@ rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st);
 // Histogram (scatter = false) or scatter pass of the partitioned variant for
 // key/value shapes, streaming; grid = p.fixed_grid CTAs in both passes.
 bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot);
+// Grid of both streaming passes (CTAs resident at once on all SMs).
+uint32_t gb_ppass_stream_grid();
 rel_status gb_launch_ppass_stream(const GbParams& p, int shape, bool scatter, cudaStream_t st);
+// Level 2 of the streaming scatter (part_bits > PART_L1_BITS): recs1 -> recs.
+rel_status gb_launch_part_l2(const GbParams& p, cudaStream_t st);
 // Aggregate-array width the kernel for a shape is compiled with.
 int gb_shape_width(int shape);
 // Shared-memory bytes of the per-CTA tables (before the staging ring).

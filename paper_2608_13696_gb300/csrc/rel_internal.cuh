@@ -231,7 +231,8 @@ enum KernelId : int {
   K_BATCH_B = 14,
   K_GB_STREAM = 15,
   K_HLL = 16,
-  K_COUNT_IDS = 17
+  K_GB_PL2 = 17,
+  K_COUNT_IDS = 18
 };
 // Bracket one launch: counts it and, while profiling, records events.
 void launch_begin(int kernel_id, cudaStream_t st);

@@ -287,23 +287,32 @@ __global__ void __launch_bounds__(ST_BLOCK, 6) gb_stream_k(const __grid_constant
 }
 
 // Partitioned variant, passes 1 and 2, streaming: a CTA counts its rows per
-// partition (pass 1), then -- after the scan turned the counts into
-// positions -- writes each row as a (key, value) record at its partition's
-// next position for this CTA (pass 2).  Pinned hot keys never become
-// records: pass 2 aggregates them in thread-private words and folds them
-// into the spill table.  INT64_MIN rows go to the side accumulator in pass 2.
-// Both passes cover the rows in the same order with the same grid, so every
-// CTA's positions are exactly the ones it counted.
-constexpr int SP_BLOCK = 512;
-// cold-partition positions: with at most 2^SCATTER_MATCH_BITS partitions a
-// warp's rows often share one, and one shared-cursor claim per partition
-// present in the warp (match) saves atomics on few addresses; above that
-// nearly every row has a partition of its own and each row claims its own
-// position (measured on 2e8 Zipf rows in 16384 partitions: 3.5 vs 3.7 ms)
-constexpr uint32_t SCATTER_MATCH_BITS = 10;
+// partition (pass 1); after the scan, pass 2 writes each row as a (key,
+// value) record.  Pinned hot keys never become records: pass 2 aggregates
+// them in thread-private words and folds them into the spill table.  INT64_MIN
+// rows go to the side accumulator in pass 2.
+//
+// Writing every record to its own partition costs one L2 write transaction
+// per 16-byte record (measured: ~3.5 ms for 1.4e8 records, at any partition
+// count from 256 to 16384).  So pass 2 sorts each chunk of SP_TILE records
+// by level-1 bin (at most 2^PART_L1_BITS bins of consecutive partitions) in
+// shared memory, claims each bin's run with one atomic on the bin's cursor
+// and writes the runs contiguously; a second pass (gb_part_l2_k) does the
+// same for the partitions inside each bin.  Record order inside a partition
+// is arbitrary, which the aggregation does not see.
+// Two 256-thread CTAs per SM: while one waits at a barrier of its sort, the
+// other streams.
+constexpr int SP_BLOCK = 256;
+constexpr int SP_MIN_BLOCKS = 2;
+constexpr int SP_TILE = SP_BLOCK * ST_U;  // rows of one chunk, records sorted at once
+constexpr int SP_BINS = 1 << PART_L1_BITS;
+static_assert(SP_BLOCK >= SP_BINS, "one thread per level-1 bin");
+// shared memory of pass 2 after the pinned words: bin counts, local and
+// global bases, bin ends, warp sums, then the tile's records and their bins
+constexpr size_t SP_SORT_SMEM = 4 * 4 * SP_BINS + 64 + 16 * SP_TILE + SP_TILE;
 
 template <class KT, int NA, bool PIN, bool SCATTER>
-__global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_constant__ GbParams p) {
+__global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(const __grid_constant__ GbParams p) {
   extern __shared__ __align__(16) uint8_t sm[];
   constexpr int PM = pin_max<NA>();
   uint64_t* pk = (uint64_t*)sm;
@@ -311,9 +320,21 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
   uint64_t* pkd = (uint64_t*)(sm + 288);
   unsigned long long* csum = (unsigned long long*)(sm + 416);
   uint64_t* acc = (uint64_t*)(sm + 416 + 8 * ST_PIN_LIMIT * 4);
-  unsigned int* ctr = (unsigned int*)(acc + ((PIN && SCATTER) ? PM * NA * SP_BLOCK : 0));
+  uint8_t* const rest = (uint8_t*)(acc + ((PIN && SCATTER) ? PM * NA * SP_BLOCK : 0));
+  unsigned int* ctr = (unsigned int*)rest;  // pass 1: [P] counts
+  // pass 2
+  unsigned int* cnt1 = (unsigned int*)rest;
+  unsigned int* lb = cnt1 + SP_BINS;
+  unsigned int* gb1 = lb + SP_BINS;
+  unsigned int* end1 = gb1 + SP_BINS;
+  unsigned int* wsum = end1 + SP_BINS;
+  PartRec* recbuf = (PartRec*)(wsum + 16);
+  uint8_t* slot_bin = (uint8_t*)(recbuf + SP_TILE);
   const int tid = threadIdx.x;
   const uint32_t P = 1u << p.part_bits;
+  const uint32_t shift1 = p.part_bits > PART_L1_BITS ? p.part_bits - PART_L1_BITS : 0;
+  const uint32_t B1 = P >> shift1;  // level-1 bins
+  PartRec* const out1 = shift1 ? p.recs1 : p.recs;
   const uint32_t tmask = p.tiny_slots - 1;
   if (PIN) {
     if (tid < 32) {
@@ -329,15 +350,13 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
       for (int i = tid; i < PM * NA; i += SP_BLOCK) csum[i] = 0;
     }
   }
-  for (uint32_t i = tid; i < P; i += SP_BLOCK)
-    ctr[i] = SCATTER ? (unsigned int)(p.part_start[i] + p.hist[(size_t)i * p.fixed_grid + blockIdx.x])
-                     : 0u;
-  uint32_t* hotb = (uint32_t*)(ctr + P);  // [P / 32] copy of the hot-partition bits
-  if (SCATTER)
-    for (uint32_t i = tid; i < (P + 31) / 32; i += SP_BLOCK) hotb[i] = p.hot[i];
-  const unsigned long long total = SCATTER ? p.part_start[P] : 0;
-  const int lane = tid & 31;
-  const unsigned lanes_below = (1u << lane) - 1u;
+  if (!SCATTER) {
+    for (uint32_t i = tid; i < P; i += SP_BLOCK) ctr[i] = 0;
+  } else if (tid < (int)B1) {
+    cnt1[tid] = 0;
+    end1[tid] = (unsigned int)p.part_start[(tid + 1) << shift1];
+  }
+  const int lane = tid & 31, warp = tid >> 5;
   __syncthreads();
 
   const KT* keys = (const KT*)p.col[p.key_col[0]];
@@ -442,53 +461,59 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
       for (int j = 0; j < ST_U; ++j)
         if (recm >> j & 1) atomicAdd(&ctr[part[j]], 1u);
     } else {
-      // hot partitions: this CTA's own cursor; the others: the partition's
-      // shared cursor
-      uint32_t hw[ST_U];
+      // sort the chunk's records by level-1 bin: ranks within the bins ...
+      uint32_t rank[ST_U];
 #pragma unroll
-      for (int j = 0; j < ST_U; ++j) hw[j] = hotb[part[j] >> 5];
-      uint32_t hotm = 0;
+      for (int j = 0; j < ST_U; ++j)
+        if (recm >> j & 1) rank[j] = atomicAdd(&cnt1[part[j] >> shift1], 1u);
+      __syncthreads();
+      // ... the bins' local bases (exclusive scan over threads 0..B1-1) and
+      // one global claim per non-empty bin ...
+      const uint32_t c = tid < (int)B1 ? cnt1[tid] : 0u;
+      uint32_t incl = c;
 #pragma unroll
-      for (int j = 0; j < ST_U; ++j) hotm |= ((recm >> j & 1) && (hw[j] >> (part[j] & 31) & 1u) ? 1u : 0u) << j;
-      const uint32_t coldm = recm & ~hotm;
-      unsigned int pos[ST_U];
-#pragma unroll
-      for (int j = 0; j < ST_U; ++j) {
-        pos[j] = 0;
-        if (hotm >> j & 1) pos[j] = atomicAdd(&ctr[part[j]], 1u);
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      if (p.part_bits <= SCATTER_MATCH_BITS) {  // uniform across the grid
-        // one claim per partition present in the warp
-        unsigned grp[ST_U];
+      if (lane == 31 && warp < SP_BINS / 32) wsum[warp] = incl;
+      __syncthreads();
+      uint32_t nrec = 0, before = 0;
 #pragma unroll
-        for (int j = 0; j < ST_U; ++j) {
-          const bool cold = coldm >> j & 1;
-          grp[j] = __match_any_sync(0xffffffffu, cold ? part[j] : (0x80000000u | (unsigned)lane));
-          if (cold && lane == __ffs(grp[j]) - 1)
-            pos[j] = atomicAdd(p.cursor + part[j], (unsigned int)__popc(grp[j]));
-        }
-#pragma unroll
-        for (int j = 0; j < ST_U; ++j) {
-          const unsigned int cb = __shfl_sync(0xffffffffu, pos[j], __ffs(grp[j]) - 1);
-          if (coldm >> j & 1) pos[j] = cb + __popc(grp[j] & lanes_below);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < ST_U; ++j)
-          if (coldm >> j & 1) pos[j] = atomicAdd(p.cursor + part[j], 1u);
+      for (int w = 0; w < SP_BINS / 32; ++w) {
+        before += w < warp ? wsum[w] : 0u;
+        nrec += wsum[w];
       }
+      if (tid < (int)B1) {
+        lb[tid] = before + incl - c;
+        if (c) gb1[tid] = atomicAdd(p.cursor1 + tid, c);
+      }
+      __syncthreads();
+      // ... the records into place in shared memory ...
 #pragma unroll
       for (int j = 0; j < ST_U; ++j) {
         if (!(recm >> j & 1)) continue;
-        if (pos[j] >= total) {  // the passes disagreed: report, never write past the buffer
-          atomicOr(&p.hdr->timeout, 2u);
-          continue;
-        }
+        const uint32_t b = part[j] >> shift1;
+        const uint32_t sl = lb[b] + rank[j];
         PartRec r;
         r.ek = ek[j];
         r.val = (long long)val[j];
-        p.recs[pos[j]] = r;
+        recbuf[sl] = r;
+        slot_bin[sl] = (uint8_t)b;
       }
+      __syncthreads();
+      // ... and out: consecutive threads write consecutive records of a run
+      for (uint32_t i = tid; i < nrec; i += SP_BLOCK) {
+        const uint32_t b = slot_bin[i];
+        const uint32_t pos = gb1[b] + (i - lb[b]);
+        if (pos >= end1[b]) {  // the passes disagreed: report, never write past the bin
+          atomicOr(&p.hdr->timeout, 2u);
+          continue;
+        }
+        out1[pos] = recbuf[i];
+      }
+      if (tid < (int)B1) cnt1[tid] = 0;
+      __syncthreads();
     }
 #pragma unroll
     for (int j = 0; j < ST_U; ++j) {
@@ -533,7 +558,7 @@ __global__ void __launch_bounds__(SP_BLOCK, 1) gb_ppass_stream_k(const __grid_co
 size_t ppass_smem(int na, bool pin, bool scatter, uint32_t part_bits) {
   size_t b = 416 + 8 * ST_PIN_LIMIT * 4;
   if (pin && scatter) b += (size_t)8 * (na == 4 ? pin_max<4>() : pin_max<2>()) * na * SP_BLOCK;
-  return b + 4ull * (1u << part_bits) + (scatter ? 4ull * (((1u << part_bits) + 31) / 32) : 0);
+  return b + (scatter ? SP_SORT_SMEM : 4ull * (1u << part_bits));
 }
 
 template <class KT, int NA, bool PIN, bool SCATTER>
@@ -613,6 +638,120 @@ bool gb_stream_eligible(const GbParams& p, int shape, int n_hot) {
   return stream_smem(na, pin, p.smem_slots != 0, p.smem_slots) <= 80 * 1024;
 }
 
+// Level 2 of the streaming scatter: every tile of PART_TILE level-1 records
+// (tiles never straddle a bin) is sorted by partition inside its bin in
+// shared memory; each partition's run is claimed with one atomic on the
+// partition's cursor and written contiguously.  Persistent grid; tile t
+// belongs to the last bin b with l2_tiles[b] <= t.
+constexpr int L2_BLOCK = 512;
+constexpr int L2_U = PART_TILE / L2_BLOCK;
+constexpr int L2_MAX_SUB = 1 << (PART_MAX_BITS - PART_L1_BITS);
+constexpr size_t L2_SMEM = 16 * PART_TILE + PART_TILE;
+
+__global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constant__ GbParams p) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  PartRec* recbuf = (PartRec*)sm;
+  uint8_t* slot_bin = sm + 16 * PART_TILE;
+  __shared__ unsigned int tp[SP_BINS + 1];
+  __shared__ unsigned int cnt[L2_MAX_SUB], lb[L2_MAX_SUB], gb[L2_MAX_SUB], endp[L2_MAX_SUB];
+  __shared__ unsigned int wsum[L2_MAX_SUB / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t shift1 = p.part_bits - PART_L1_BITS;  // > 0: launched only then
+  const uint32_t B1 = 1u << PART_L1_BITS;
+  const uint32_t B2 = 1u << shift1;
+  for (uint32_t i = tid; i <= B1; i += L2_BLOCK) tp[i] = p.l2_tiles[i];
+  if (tid < (int)B2) cnt[tid] = 0;
+  __syncthreads();
+  const uint32_t T = tp[B1];
+  for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+    uint32_t lo = 0, hi = B1;  // tp[lo] <= t < tp[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (tp[mid] <= t) lo = mid; else hi = mid;
+    }
+    const uint32_t first = lo << shift1;  // first partition of the bin
+    const unsigned long long s1 = p.part_start[first];
+    const unsigned long long e1 = p.part_start[first + B2];
+    const unsigned long long t0 = s1 + (unsigned long long)(t - tp[lo]) * PART_TILE;
+    const unsigned long long t1 = t0 + PART_TILE < e1 ? t0 + PART_TILE : e1;
+    if (tid < (int)B2) endp[tid] = (unsigned int)p.part_start[first + tid + 1];
+    PartRec r[L2_U];
+    uint32_t sr[L2_U];  // partition within the bin | rank within it << 8
+#pragma unroll
+    for (int u = 0; u < L2_U; ++u) {
+      const unsigned long long i = t0 + (unsigned long long)u * L2_BLOCK + tid;
+      sr[u] = 0;
+      if (i < t1) {
+        const longlong2 v = __ldcs((const longlong2*)(p.recs1 + i));
+        r[u].ek = (unsigned long long)v.x;
+        r[u].val = v.y;
+        sr[u] = part_of((uint64_t)v.x, p.part_bits) & (B2 - 1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < L2_U; ++u)
+      if (t0 + (unsigned long long)u * L2_BLOCK + tid < t1) sr[u] |= atomicAdd(&cnt[sr[u]], 1u) << 8;
+    __syncthreads();
+    const uint32_t c = tid < (int)B2 ? cnt[tid] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31 && warp < L2_MAX_SUB / 32) wsum[warp] = incl;
+    __syncthreads();
+    if (tid < (int)B2) {
+      uint32_t before = 0;
+      for (int w = 0; w < warp; ++w) before += wsum[w];
+      lb[tid] = before + incl - c;
+      if (c) gb[tid] = atomicAdd(p.cursor + first + tid, c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < L2_U; ++u) {
+      if (t0 + (unsigned long long)u * L2_BLOCK + tid >= t1) continue;
+      const uint32_t sub = sr[u] & 0xFFu;
+      const uint32_t sl = lb[sub] + (sr[u] >> 8);
+      recbuf[sl] = r[u];
+      slot_bin[sl] = (uint8_t)sub;
+    }
+    __syncthreads();
+    const uint32_t nrec = (uint32_t)(t1 - t0);
+    for (uint32_t i = tid; i < nrec; i += L2_BLOCK) {
+      const uint32_t b = slot_bin[i];
+      const uint32_t pos = gb[b] + (i - lb[b]);
+      if (pos >= endp[b]) {  // the passes disagreed: report, never write past the partition
+        atomicOr(&p.hdr->timeout, 2u);
+        continue;
+      }
+      p.recs[pos] = recbuf[i];
+    }
+    if (tid < (int)B2) cnt[tid] = 0;
+    __syncthreads();
+  }
+}
+
+rel_status gb_launch_part_l2(const GbParams& p, cudaStream_t st) {
+  if (p.part_bits <= PART_L1_BITS || p.part_bits > PART_MAX_BITS || !p.recs1)
+    return relhost::set_error("group-by: level-2 scatter needs more than 2^%d partitions", PART_L1_BITS),
+           REL_E_INVALID;
+  cudaError_t e = cudaFuncSetAttribute(gb_part_l2_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L2_SMEM);
+  if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(level-2 scatter)");
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gb_part_l2_k, L2_BLOCK, L2_SMEM);
+  if (e != cudaSuccess || occ < 1) return relhost::cuda_fail(e, "occupancy(level-2 scatter)");
+  const int grid = relhost::device_sms() * occ;
+  relhost::launch_begin(relhost::K_GB_PL2, st);
+  gb_part_l2_k<<<grid, L2_BLOCK, L2_SMEM, st>>>(p);
+  relhost::launch_end(relhost::K_GB_PL2, st);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(level-2 scatter)");
+}
+
+uint32_t gb_ppass_stream_grid() { return (uint32_t)relhost::device_sms() * SP_MIN_BLOCKS; }
+
 bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot) {
   const bool kv = shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 || shape == SHAPE_KV2_64 ||
                   shape == SHAPE_KV2_32;
@@ -620,7 +759,8 @@ bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot) {
   const int na = (shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32) ? 4 : 2;
   const int pmax = na == 4 ? pin_max<4>() : pin_max<2>();
   if (p.tiny_slots && !(p.tiny_frozen && p.tiny_slots <= 32 && n_hot <= pmax)) return false;
-  return ppass_smem(na, p.tiny_slots != 0, true, p.part_bits) <= 200 * 1024;
+  return ppass_smem(na, p.tiny_slots != 0, true, p.part_bits) * SP_MIN_BLOCKS <= 227 * 1024 &&
+         ppass_smem(na, p.tiny_slots != 0, false, p.part_bits) * SP_MIN_BLOCKS <= 227 * 1024;
 }
 
 rel_status gb_launch_ppass_stream(const GbParams& p, int shape, bool scatter, cudaStream_t st) {

@@ -34,6 +34,7 @@ SOURCES = {
     "gb_main_keyset": ["distinct.cu", "api.cu"],
     "gb_part_hist": ["stream.cu", "api.cu"],
     "gb_part_scatter": ["stream.cu", "api.cu"],
+    "gb_part_l2": ["stream.cu", "api.cu"],
     "gb_part_scan": ["groupby.cu", "api.cu"],
     "gb_part_agg": ["groupby.cu", "api.cu"],
     "gb_compact": ["groupby.cu", "api.cu"],

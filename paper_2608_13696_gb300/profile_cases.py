@@ -6,8 +6,8 @@ run, each launching the kernels of interest a few times at most.
 CASE (inputs seeded and synthetic, as in the bench):
   distinct  exact distinct count of 5e7 Zipf(1.1) keys (distinct_k)
   part      partitioned group-by of 5e7 Zipf(1.1) key/value rows with the
-            sample sketch's pins (histogram, scan, scatter, aggregation,
-            compaction)
+            sample sketch's pins (histogram, scan, two scatter levels,
+            aggregation, compaction)
   stream    streaming group-by of 5e7 four-key rows with pinned keys (gb_stream)
   join      join build of 1e6 unique keys and probe of 1.6e7 keys (90 % hits)
   lineitem  fused filter + group-by of 2e7 lineitem rows: exact count (staged
@@ -63,6 +63,7 @@ def case_part(n=50_000_000):
     recs = int(n - torch.isin(kd, hot).sum().item())  # rows written as partition records
     out = k.numel() * 8 * (1 + len(aggs))
     return {"gb_part_hist": (n, "rows", 8 * n), "gb_part_scatter": (n, "rows", 16 * n + 16 * recs),
+            "gb_part_l2": (n, "rows", 32 * recs),
             "gb_part_scan": (n, "rows", None), "gb_part_agg": (n, "rows", 16 * recs + out),
             "gb_compact": (n, "rows", out), "records": recs, "groups": k.numel()}
 

@@ -86,3 +86,18 @@ def test_bad_partition_plan_rejected():
     with pytest.raises(rel.RelError) as e:
         rel.groupby(qc, plan=plan)
     assert e.value.status == rel.REL_E_INVALID
+
+
+@pytest.mark.parametrize("bits", [8, 9, 11, 14])
+def test_two_level_scatter(bits):
+    # above 2^8 partitions the scatter runs in two levels (bins of
+    # 2^(bits-8) partitions, then partitions); skewed keys make bins of many
+    # tiles next to empty ones
+    keys, vals = synth.zipf_kv(1_000_003, seed=18 + bits, n_ranks=400_000)
+    keys[::113] = np.iinfo(np.int64).min
+
+    def force(plan):
+        plan.part_bits = bits
+        plan.smem_slots = max(256, min(4096, 1 << (20 - bits)))
+
+    run(oracle.kv_query(keys, vals), rel.PLAN_EXACT | rel.PLAN_SKETCH, force)
