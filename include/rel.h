@@ -238,7 +238,8 @@ uint64_t rel_groupby_ws_bytes(int64_t slots, int32_t n_aggs);
 
 /* Device bytes rel_groupby_agg needs for a (possibly edited) plan over
  * n_rows rows with n_aggs aggregates -- the partitioned variant also keeps a
- * 16-byte record per row. */
+ * 16-byte record per row, and a second one per row above 256 partitions
+ * (its scatter runs in two levels). */
 uint64_t rel_plan_ws_bytes(const rel_plan* plan, int32_t n_aggs, int64_t n_rows);
 
 /* Plan and run in one call, with the learned planner's overflow fallback:
