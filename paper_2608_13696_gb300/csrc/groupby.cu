@@ -262,6 +262,19 @@ __device__ __forceinline__ void red_words(const GbParams& p, unsigned long long*
 template <class S, bool COUNT32 = false>
 __device__ __forceinline__ void red_words_smem(const GbParams& p, unsigned long long* w,
                                                const Vals<S::A>& x) {
+  if constexpr (COUNT32 && !S::RT && S::A == 4) {
+    // (sum, count, min, max) of a 32-byte slot: the MIN / MAX pair is read
+    // with one 16-byte load (w is 32-byte aligned)
+    sadd64(w, x.v[0]);
+    atomicAdd((unsigned int*)(w + 1), (unsigned int)x.v[1]);
+    unsigned long long mn, mx;
+    asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(mn), "=l"(mx)
+                 : "r"(smem_u32(w + 2)));
+    if ((unsigned long long)x.v[2] > mn) atomicMax(w + 2, (unsigned long long)x.v[2]);
+    if ((unsigned long long)x.v[3] > mx) atomicMax(w + 3, (unsigned long long)x.v[3]);
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < S::A; ++a) {
     if (live_agg<S>(p, a)) {
@@ -964,8 +977,7 @@ __device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, uns
   gtab_update<S>(p, ek, x);
 }
 
-constexpr int PA_R = 4;        // record groups in flight per warp in the aggregation pass
-constexpr int PA_COMBINE = 6;  // lanes of the first key above which they are combined first
+constexpr int PA_R = 4;  // record groups in flight per warp in the aggregation pass
 
 // Pass 3: each CTA aggregates whole partitions in a shared-memory table of
 // p.smem_slots slots and writes their groups straight to the output (warp
@@ -1005,65 +1017,26 @@ __global__ void __launch_bounds__(GB_BLOCK) gb_part_agg(const __grid_constant__ 
     __syncthreads();
     {
       // each warp takes 32 consecutive records at a time, PA_R such groups
-      // loaded before any is used (the pass is bound by load latency); when
-      // more than PA_COMBINE lanes hold the warp's first key (under skew,
-      // usually the partition's heavy key) its rows are combined in registers
-      // first (0 is every word's identity) and applied once, every other row
-      // goes to the table on its own
+      // loaded before any is used (the pass is bound by load latency).  Lanes
+      // of one key are not combined in registers first: on the partitions of
+      // skewed keys that did not cost less than the serialised shared-memory
+      // atomics it saves (2e8 Zipf(1.1) rows: 2.0 -> 1.9 ms without it)
       const int warp = threadIdx.x >> 5;
       for (unsigned long long b00 = beg + (unsigned long long)warp * 32 * PA_R; b00 < end;
            b00 += (unsigned long long)GB_BLOCK * PA_R) {
-       longlong2 rec[PA_R];
+        longlong2 rec[PA_R];
 #pragma unroll
-       for (int rr = 0; rr < PA_R; ++rr) {
-         const unsigned long long i = b00 + (unsigned long long)rr * 32 + lane;
-         rec[rr] = i < end ? __ldcs((const longlong2*)(p.recs + i)) : make_longlong2(0, 0);
-       }
+        for (int rr = 0; rr < PA_R; ++rr) {
+          const unsigned long long i = b00 + (unsigned long long)rr * 32 + lane;
+          rec[rr] = i < end ? __ldcs((const longlong2*)(p.recs + i)) : make_longlong2(0, 0);
+        }
 #pragma unroll
-       for (int rr = 0; rr < PA_R; ++rr) {
-        const unsigned long long b0 = b00 + (unsigned long long)rr * 32;
-        if (b0 >= end) break;  // uniform across the warp
-        const unsigned long long i = b0 + lane;
-        const bool valid = i < end;
-        Vals<A> x;
-        uint64_t ek = 0;
-        if (valid) {
-          ek = (uint64_t)rec[rr].x;
+        for (int rr = 0; rr < PA_R; ++rr) {
+          if (b00 + (unsigned long long)rr * 32 + lane >= end) continue;
+          Vals<A> x;
           S::from_val((uint64_t)rec[rr].y, x);
-        } else {
-#pragma unroll
-          for (int a = 0; a < A; ++a) x.v[a] = 0;
+          part_insert<S>(p, tk, ta, TS, (uint64_t)rec[rr].x, x, &ovf);
         }
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        const int ld = __ffs(vm) - 1;  // vm != 0: b0 < end
-        const uint64_t key = __shfl_sync(0xffffffffu, ek, ld);
-        const bool mine = valid && ek == key;
-        const unsigned m = __ballot_sync(0xffffffffu, mine);
-        // combining costs ~3 x 5 shuffle rounds; worth it only when many lanes
-        // would otherwise serialise on one shared-memory word
-        const bool combine = __popc(m) > PA_COMBINE;  // uniform across the warp
-        if (combine) {
-          // the first key's words over its lanes; its count is the lanes'
-          // number (word 1 of the key/value shapes counts rows)
-#pragma unroll
-          for (int a = 0; a < A; ++a) {
-            if (a == 1 && !S::RT) continue;
-            const bool um = is_umax<S>(p, a);
-            uint64_t v = mine ? x.v[a] : 0ull;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-              const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
-              v = um ? (v > w ? v : w) : v + w;
-            }
-            if (lane == ld) x.v[a] = v;
-          }
-          if (!S::RT && lane == ld) x.v[1] = (uint64_t)__popc(m);
-        }
-        // one insert per lane in one converged call: the first key's lane
-        // brings the combined words, the other keys' lanes their own row,
-        // the first key's other lanes nothing
-        if (valid && (!combine || !mine || lane == ld)) part_insert<S>(p, tk, ta, TS, ek, x, &ovf);
-       }
       }
     }
     __syncthreads();
