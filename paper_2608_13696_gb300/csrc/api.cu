@@ -97,7 +97,6 @@ using namespace rel;
 
 constexpr int32_t TABLE_MAGIC = 0x4a4f494e;  // "JOIN"
 constexpr int64_t MAX_INDEX_ROWS = 2147483647;
-constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 int elem_size(int32_t t) { return t == REL_U8 ? 1 : t == REL_I32 ? 4 : 8; }
 int elem_bits(int32_t t) { return 8 * elem_size(t); }
@@ -472,9 +471,9 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   }
   rel_status r;
   if (!plan->tile_rows && gb_ppass_stream_eligible(p, shape, plan->n_hot)) {
-    // the CTAs that fit on the SMs at once (the pinned keys' thread-private
-    // words fill most of their shared memory)
-    p.fixed_grid = gb_ppass_stream_grid() < PART_MAX_GRID ? gb_ppass_stream_grid() : PART_MAX_GRID;
+    // the histogram's CTAs: as many as fit on the SMs at once
+    p.fixed_grid = gb_ppass_stream_grid(p, shape, PART_MAX_GRID);
+    if (p.fixed_grid < 1) return set_error("group-by: partition histogram does not fit"), REL_E_UNSUPPORTED;
     if ((r = gb_launch_ppass_stream(p, shape, false, st))) return r;
     if ((r = gb_launch_part_scan(p, st))) return r;
     if ((r = gb_launch_ppass_stream(p, shape, true, st))) return r;

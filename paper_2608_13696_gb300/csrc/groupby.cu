@@ -273,20 +273,20 @@ __device__ __forceinline__ void red_words_smem(const GbParams& p, unsigned long 
                  : "r"(smem_u32(w + 2)));
     if ((unsigned long long)x.v[2] > mn) atomicMax(w + 2, (unsigned long long)x.v[2]);
     if ((unsigned long long)x.v[3] > mx) atomicMax(w + 3, (unsigned long long)x.v[3]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int a = 0; a < S::A; ++a) {
-    if (live_agg<S>(p, a)) {
-      if (COUNT32 && a == 1) {
-        // key/value shapes: word 1 counts rows; below 2^32 rows per table
-        // (a partitioned input has fewer) a 32-bit add on its low half is exact
-        atomicAdd((unsigned int*)(w + 1), (unsigned int)x.v[1]);
-      } else if (is_umax<S>(p, a)) {
-        if ((unsigned long long)x.v[a] > *(volatile unsigned long long*)(w + a))
-          atomicMax(w + a, (unsigned long long)x.v[a]);
-      } else {
-        sadd64(w + a, x.v[a]);
+    for (int a = 0; a < S::A; ++a) {
+      if (live_agg<S>(p, a)) {
+        if (COUNT32 && a == 1) {
+          // key/value shapes: word 1 counts rows; below 2^32 rows per table
+          // (a partitioned input has fewer) a 32-bit add on its low half is exact
+          atomicAdd((unsigned int*)(w + 1), (unsigned int)x.v[1]);
+        } else if (is_umax<S>(p, a)) {
+          if ((unsigned long long)x.v[a] > *(volatile unsigned long long*)(w + a))
+            atomicMax(w + a, (unsigned long long)x.v[a]);
+        } else {
+          sadd64(w + a, x.v[a]);
+        }
       }
     }
   }

@@ -132,8 +132,9 @@ rel_status gb_launch_stream(const GbParams& p, int shape, cudaStream_t st);
 // Histogram (scatter = false) or scatter pass of the partitioned variant for
 // key/value shapes, streaming; grid = p.fixed_grid CTAs in both passes.
 bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot);
-// Grid of both streaming passes (CTAs resident at once on all SMs).
-uint32_t gb_ppass_stream_grid();
+// Grid of the streaming histogram pass: the CTAs resident at once on all
+// SMs, at most cap (0 when the pass cannot launch).
+uint32_t gb_ppass_stream_grid(const GbParams& p, int shape, uint32_t cap);
 rel_status gb_launch_ppass_stream(const GbParams& p, int shape, bool scatter, cudaStream_t st);
 // Level 2 of the streaming scatter (part_bits > PART_L1_BITS): recs1 -> recs.
 rel_status gb_launch_part_l2(const GbParams& p, cudaStream_t st);

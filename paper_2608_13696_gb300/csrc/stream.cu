@@ -467,8 +467,9 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
       for (int j = 0; j < ST_U; ++j)
         if (recm >> j & 1) rank[j] = atomicAdd(&cnt1[part[j] >> shift1], 1u);
       __syncthreads();
-      // ... the bins' local bases (exclusive scan over threads 0..B1-1) and
-      // one global claim per non-empty bin ...
+      // ... the bins' local bases (exclusive scan over threads 0..B1-1), one
+      // global claim per non-empty bin, and the counts cleared for the next
+      // chunk (every thread has read its count by the barrier before) ...
       const uint32_t c = tid < (int)B1 ? cnt1[tid] : 0u;
       uint32_t incl = c;
 #pragma unroll
@@ -487,6 +488,7 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
       if (tid < (int)B1) {
         lb[tid] = before + incl - c;
         if (c) gb1[tid] = atomicAdd(p.cursor1 + tid, c);
+        cnt1[tid] = 0;
       }
       __syncthreads();
       // ... the records into place in shared memory ...
@@ -502,7 +504,9 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
         slot_bin[sl] = (uint8_t)b;
       }
       __syncthreads();
-      // ... and out: consecutive threads write consecutive records of a run
+      // ... and out: consecutive threads write consecutive records of a run.
+      // No barrier after: the next chunk touches only the cleared counts
+      // before its first barrier, which every thread reaches after this.
       for (uint32_t i = tid; i < nrec; i += SP_BLOCK) {
         const uint32_t b = slot_bin[i];
         const uint32_t pos = gb1[b] + (i - lb[b]);
@@ -512,8 +516,6 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
         }
         out1[pos] = recbuf[i];
       }
-      if (tid < (int)B1) cnt1[tid] = 0;
-      __syncthreads();
     }
 #pragma unroll
     for (int j = 0; j < ST_U; ++j) {
@@ -561,15 +563,34 @@ size_t ppass_smem(int na, bool pin, bool scatter, uint32_t part_bits) {
   return b + (scatter ? SP_SORT_SMEM : 4ull * (1u << part_bits));
 }
 
+// CTAs of a pass that fit on the SMs at once (at most cap), or 0.
+template <class KT, int NA, bool PIN, bool SCATTER>
+uint32_t ppass_grid(const GbParams& p, uint32_t cap) {
+  auto kern = gb_ppass_stream_k<KT, NA, PIN, SCATTER>;
+  const size_t smem = ppass_smem(NA, PIN, SCATTER, p.part_bits);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SP_BLOCK, smem) != cudaSuccess)
+    return 0;
+  const uint32_t g = (uint32_t)relhost::device_sms() * (uint32_t)(occ > 0 ? occ : 0);
+  return g < cap ? g : cap;
+}
+
+// The histogram pass runs p.fixed_grid CTAs (its counts are laid out per
+// CTA); the scatter pass, whose positions come from the bins' cursors, runs
+// as many CTAs as fit.
 template <class KT, int NA, bool PIN, bool SCATTER>
 rel_status launch_ppass(const GbParams& p, cudaStream_t st) {
   auto kern = gb_ppass_stream_k<KT, NA, PIN, SCATTER>;
   const size_t smem = ppass_smem(NA, PIN, SCATTER, p.part_bits);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return relhost::cuda_fail(e, "cudaFuncSetAttribute(partition pass)");
+  const uint32_t grid = SCATTER ? ppass_grid<KT, NA, PIN, SCATTER>(p, 1u << 16) : p.fixed_grid;
+  if (grid < 1) return relhost::set_error("group-by: partition pass does not fit"), REL_E_UNSUPPORTED;
   const int id = SCATTER ? relhost::K_GB_PSCATTER : relhost::K_GB_PHIST;
   relhost::launch_begin(id, st);
-  kern<<<p.fixed_grid, SP_BLOCK, smem, st>>>(p);
+  kern<<<grid, SP_BLOCK, smem, st>>>(p);
   relhost::launch_end(id, st);
   e = cudaGetLastError();
   return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(partition pass)");
@@ -654,7 +675,6 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
   uint8_t* slot_bin = sm + 16 * PART_TILE;
   __shared__ unsigned int tp[SP_BINS + 1];
   __shared__ unsigned int cnt[L2_MAX_SUB], lb[L2_MAX_SUB], gb[L2_MAX_SUB], endp[L2_MAX_SUB];
-  __shared__ unsigned int wsum[L2_MAX_SUB / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t shift1 = p.part_bits - PART_L1_BITS;  // > 0: launched only then
   const uint32_t B1 = 1u << PART_L1_BITS;
@@ -674,7 +694,6 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
     const unsigned long long e1 = p.part_start[first + B2];
     const unsigned long long t0 = s1 + (unsigned long long)(t - tp[lo]) * PART_TILE;
     const unsigned long long t1 = t0 + PART_TILE < e1 ? t0 + PART_TILE : e1;
-    if (tid < (int)B2) endp[tid] = (unsigned int)p.part_start[first + tid + 1];
     PartRec r[L2_U];
     uint32_t sr[L2_U];  // partition within the bin | rank within it << 8
 #pragma unroll
@@ -692,20 +711,35 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
     for (int u = 0; u < L2_U; ++u)
       if (t0 + (unsigned long long)u * L2_BLOCK + tid < t1) sr[u] |= atomicAdd(&cnt[sr[u]], 1u) << 8;
     __syncthreads();
-    const uint32_t c = tid < (int)B2 ? cnt[tid] : 0u;
-    uint32_t incl = c;
+    // warp 0: local bases, one claim per non-empty partition, partition ends,
+    // counts cleared for the next tile
+    if (warp == 0) {
+      constexpr int PER = L2_MAX_SUB / 32;
+      uint32_t cb[PER], sum = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31 && warp < L2_MAX_SUB / 32) wsum[warp] = incl;
-    __syncthreads();
-    if (tid < (int)B2) {
-      uint32_t before = 0;
-      for (int w = 0; w < warp; ++w) before += wsum[w];
-      lb[tid] = before + incl - c;
-      if (c) gb[tid] = atomicAdd(p.cursor + first + tid, c);
+      for (int k = 0; k < PER; ++k) {
+        const uint32_t bn = lane * PER + k;
+        cb[k] = bn < B2 ? cnt[bn] : 0u;
+        sum += cb[k];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint32_t run = incl - sum;
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const uint32_t bn = lane * PER + k;
+        if (bn < B2) {
+          lb[bn] = run;
+          if (cb[k]) gb[bn] = atomicAdd(p.cursor + first + bn, cb[k]);
+          endp[bn] = (unsigned int)p.part_start[first + bn + 1];
+          cnt[bn] = 0;
+        }
+        run += cb[k];
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -717,6 +751,8 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
       slot_bin[sl] = (uint8_t)sub;
     }
     __syncthreads();
+    // no barrier after the writes: the next tile touches only the cleared
+    // counts before its first barrier
     const uint32_t nrec = (uint32_t)(t1 - t0);
     for (uint32_t i = tid; i < nrec; i += L2_BLOCK) {
       const uint32_t b = slot_bin[i];
@@ -727,8 +763,6 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
       }
       p.recs[pos] = recbuf[i];
     }
-    if (tid < (int)B2) cnt[tid] = 0;
-    __syncthreads();
   }
 }
 
@@ -750,7 +784,20 @@ rel_status gb_launch_part_l2(const GbParams& p, cudaStream_t st) {
   return e == cudaSuccess ? REL_OK : relhost::cuda_fail(e, "launch(level-2 scatter)");
 }
 
-uint32_t gb_ppass_stream_grid() { return (uint32_t)relhost::device_sms() * SP_MIN_BLOCKS; }
+uint32_t gb_ppass_stream_grid(const GbParams& p, int shape, uint32_t cap) {
+  const bool pin = p.tiny_frozen && p.tiny_slots;
+  switch (shape) {
+    case SHAPE_KV4_64:
+      return pin ? ppass_grid<int64_t, 4, true, false>(p, cap) : ppass_grid<int64_t, 4, false, false>(p, cap);
+    case SHAPE_KV4_32:
+      return pin ? ppass_grid<int32_t, 4, true, false>(p, cap) : ppass_grid<int32_t, 4, false, false>(p, cap);
+    case SHAPE_KV2_64:
+      return pin ? ppass_grid<int64_t, 2, true, false>(p, cap) : ppass_grid<int64_t, 2, false, false>(p, cap);
+    case SHAPE_KV2_32:
+      return pin ? ppass_grid<int32_t, 2, true, false>(p, cap) : ppass_grid<int32_t, 2, false, false>(p, cap);
+    default: return 0;
+  }
+}
 
 bool gb_ppass_stream_eligible(const GbParams& p, int shape, int n_hot) {
   const bool kv = shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 || shape == SHAPE_KV2_64 ||
