@@ -1526,6 +1526,8 @@ rel_status rel_groupby_agg(const rel_groupby_desc* d, const rel_plan* plan, void
   HostHeader h;
   if ((r = read_header(ws, &h, st))) return r;
   *n_groups_host = (int64_t)h.n_out;
+  if (h.timeout & 2u)  // a partition pass found a count it did not expect; nothing was written past
+    return set_error("group-by: the partition passes disagreed on a partition's size"), REL_E_CUDA;
   if (h.timeout) return set_error("group-by: a device wait timed out"), REL_E_TIMEOUT;
   if (h.overflow) {
     *n_groups_host = -1;

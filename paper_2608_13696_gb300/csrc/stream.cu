@@ -306,6 +306,7 @@ constexpr int SP_BLOCK = 256;
 constexpr int SP_MIN_BLOCKS = 2;
 constexpr int SP_TILE = SP_BLOCK * ST_U;  // rows of one chunk, records sorted at once
 constexpr int SP_BINS = 1 << PART_L1_BITS;
+constexpr int SP_BAD = 15;  // wsum[SP_BAD] != 0: a claim overran its bin
 static_assert(SP_BLOCK >= SP_BINS, "one thread per level-1 bin");
 // shared memory of pass 2 after the pinned words: bin counts, local and
 // global bases, bin ends, warp sums, then the tile's records and their bins
@@ -352,9 +353,12 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
   }
   if (!SCATTER) {
     for (uint32_t i = tid; i < P; i += SP_BLOCK) ctr[i] = 0;
-  } else if (tid < (int)B1) {
-    cnt1[tid] = 0;
-    end1[tid] = (unsigned int)p.part_start[(tid + 1) << shift1];
+  } else {
+    if (tid < (int)B1) {
+      cnt1[tid] = 0;
+      end1[tid] = (unsigned int)p.part_start[(tid + 1) << shift1];
+    }
+    if (tid == 0) wsum[SP_BAD] = 0;
   }
   const int lane = tid & 31, warp = tid >> 5;
   __syncthreads();
@@ -487,7 +491,17 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
       }
       if (tid < (int)B1) {
         lb[tid] = before + incl - c;
-        if (c) gb1[tid] = atomicAdd(p.cursor1 + tid, c);
+        // output position of local slot i of this bin: i + delta (mod 2^32);
+        // a claim past the bin's end (the passes disagreed) voids the call and
+        // stops this CTA's writes
+        if (c) {
+          const uint32_t g = atomicAdd(p.cursor1 + tid, c);
+          if (g + c > end1[tid]) {
+            atomicOr(&p.hdr->timeout, 2u);
+            wsum[SP_BAD] = 1;
+          }
+          gb1[tid] = g - (before + incl - c);
+        }
         cnt1[tid] = 0;
       }
       __syncthreads();
@@ -507,15 +521,8 @@ __global__ void __launch_bounds__(SP_BLOCK, SP_MIN_BLOCKS) gb_ppass_stream_k(con
       // ... and out: consecutive threads write consecutive records of a run.
       // No barrier after: the next chunk touches only the cleared counts
       // before its first barrier, which every thread reaches after this.
-      for (uint32_t i = tid; i < nrec; i += SP_BLOCK) {
-        const uint32_t b = slot_bin[i];
-        const uint32_t pos = gb1[b] + (i - lb[b]);
-        if (pos >= end1[b]) {  // the passes disagreed: report, never write past the bin
-          atomicOr(&p.hdr->timeout, 2u);
-          continue;
-        }
-        out1[pos] = recbuf[i];
-      }
+      if (!wsum[SP_BAD])  // uniform: never past a bin
+        for (uint32_t i = tid; i < nrec; i += SP_BLOCK) out1[i + gb1[slot_bin[i]]] = recbuf[i];
     }
 #pragma unroll
     for (int j = 0; j < ST_U; ++j) {
@@ -674,13 +681,15 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
   PartRec* recbuf = (PartRec*)sm;
   uint8_t* slot_bin = sm + 16 * PART_TILE;
   __shared__ unsigned int tp[SP_BINS + 1];
-  __shared__ unsigned int cnt[L2_MAX_SUB], lb[L2_MAX_SUB], gb[L2_MAX_SUB], endp[L2_MAX_SUB];
+  __shared__ unsigned int cnt[L2_MAX_SUB], lb[L2_MAX_SUB], gb[L2_MAX_SUB];
+  __shared__ int bad;  // a claim overran its partition: this CTA writes no more
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t shift1 = p.part_bits - PART_L1_BITS;  // > 0: launched only then
   const uint32_t B1 = 1u << PART_L1_BITS;
   const uint32_t B2 = 1u << shift1;
   for (uint32_t i = tid; i <= B1; i += L2_BLOCK) tp[i] = p.l2_tiles[i];
   if (tid < (int)B2) cnt[tid] = 0;
+  if (tid == 0) bad = 0;
   __syncthreads();
   const uint32_t T = tp[B1];
   for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -734,8 +743,14 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
         const uint32_t bn = lane * PER + k;
         if (bn < B2) {
           lb[bn] = run;
-          if (cb[k]) gb[bn] = atomicAdd(p.cursor + first + bn, cb[k]);
-          endp[bn] = (unsigned int)p.part_start[first + bn + 1];
+          if (cb[k]) {  // position of local slot i: i + delta (see the level-1 pass)
+            const uint32_t g = atomicAdd(p.cursor + first + bn, cb[k]);
+            if (g + cb[k] > (uint32_t)p.part_start[first + bn + 1]) {
+              atomicOr(&p.hdr->timeout, 2u);
+              bad = 1;
+            }
+            gb[bn] = g - run;
+          }
           cnt[bn] = 0;
         }
         run += cb[k];
@@ -754,15 +769,8 @@ __global__ void __launch_bounds__(L2_BLOCK, 2) gb_part_l2_k(const __grid_constan
     // no barrier after the writes: the next tile touches only the cleared
     // counts before its first barrier
     const uint32_t nrec = (uint32_t)(t1 - t0);
-    for (uint32_t i = tid; i < nrec; i += L2_BLOCK) {
-      const uint32_t b = slot_bin[i];
-      const uint32_t pos = gb[b] + (i - lb[b]);
-      if (pos >= endp[b]) {  // the passes disagreed: report, never write past the partition
-        atomicOr(&p.hdr->timeout, 2u);
-        continue;
-      }
-      p.recs[pos] = recbuf[i];
-    }
+    if (!bad)  // uniform: never past a partition
+      for (uint32_t i = tid; i < nrec; i += L2_BLOCK) p.recs[i + gb[slot_bin[i]]] = recbuf[i];
   }
 }
 
