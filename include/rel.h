@@ -45,7 +45,7 @@ typedef int32_t rel_status;
 #define REL_E_CAPACITY (-2)    /* output or workspace too small; see *_host    */
 #define REL_E_CUDA (-3)        /* a CUDA runtime call failed                   */
 #define REL_E_TIMEOUT (-4)     /* a bounded device-side wait gave up           */
-#define REL_E_UNSUPPORTED (-5) /* valid request outside this build's limits    */
+#define REL_E_UNSUPPORTED (-5) /* valid request outside the library's limits    */
 #define REL_E_OVERFLOW (-6)    /* hash table sized by the plan was too small   */
 
 /* column element types */

@@ -475,7 +475,7 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
     p.fixed_grid = gb_ppass_stream_grid(p, shape, PART_MAX_GRID);
     if (p.fixed_grid < 1) return set_error("group-by: partition histogram does not fit"), REL_E_UNSUPPORTED;
     if ((r = gb_launch_ppass_stream(p, shape, false, st))) return r;
-    if ((r = gb_launch_part_scan(p, st))) return r;
+    if ((r = gb_launch_part_scan(p, false, st))) return r;
     if ((r = gb_launch_ppass_stream(p, shape, true, st))) return r;
     if (p.part_bits > PART_L1_BITS && (r = gb_launch_part_l2(p, st))) return r;
     p.smem_slots = agg_slots;
@@ -490,7 +490,7 @@ rel_status run_partitioned(GbParams& p, const rel_plan* plan, int shape, const G
   if (!configure_stages(p, shape, MODE_PHIST, tma) || p.tile_rows != T)
     return set_error("group-by: partition histogram does not fit"), REL_E_UNSUPPORTED;
   if ((r = gb_launch_main(p, shape, MODE_PHIST, tma, st))) return r;
-  if ((r = gb_launch_part_scan(p, st))) return r;
+  if ((r = gb_launch_part_scan(p, true, st))) return r;
   set_stages(p, T, NS);
   if ((r = gb_launch_main(p, shape, MODE_PSCATTER, tma, st))) return r;
   p.smem_slots = agg_slots;

@@ -920,6 +920,22 @@ __global__ void __launch_bounds__(1024) gb_part_scan1(const __grid_constant__ Gb
   if (threadIdx.x == 0) p.part_start[blockIdx.x] = total;
 }
 
+// hist[part][cta] -> the partition's total in part_start[part] only (the
+// streaming passes place records by bin cursors, not by per-CTA offsets).
+// One warp per partition.
+__global__ void __launch_bounds__(256) gb_part_sum(const __grid_constant__ GbParams p) {
+  const uint32_t part = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (part >= (1u << p.part_bits)) return;  // whole warps
+  const uint32_t G = p.fixed_grid;
+  const uint32_t* h = p.hist + (size_t)part * G;
+  unsigned long long s = 0;
+  for (uint32_t i = lane; i < G; i += 32) s += h[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) p.part_start[part] = s;
+}
+
 // partition totals -> first record of each partition; part_start[P] = all.
 // Also the cursors of both scatter levels and the level-2 pass's tiles.
 __global__ void __launch_bounds__(1024) gb_part_scan2(const __grid_constant__ GbParams p) {
@@ -1263,10 +1279,13 @@ rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool tma, cuda
   });
 }
 
-rel_status gb_launch_part_scan(const GbParams& p, cudaStream_t st) {
+rel_status gb_launch_part_scan(const GbParams& p, bool cta_offsets, cudaStream_t st) {
   const uint32_t P = 1u << p.part_bits;
   relhost::launch_begin(relhost::K_GB_PSCAN, st);
-  gb_part_scan1<<<P, 1024, 0, st>>>(p);
+  if (cta_offsets)
+    gb_part_scan1<<<P, 1024, 0, st>>>(p);
+  else
+    gb_part_sum<<<(P + 7) / 8, 256, 0, st>>>(p);
   relhost::launch_end(relhost::K_GB_PSCAN, st);
   relhost::launch_begin(relhost::K_GB_PSCAN, st);
   gb_part_scan2<<<1, 1024, 0, st>>>(p);

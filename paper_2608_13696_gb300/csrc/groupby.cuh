@@ -122,8 +122,9 @@ struct GbOut {
 rel_status gb_launch_main(const GbParams& p, int shape, int mode, bool use_tma,
                           cudaStream_t st);
 rel_status gb_launch_compact(const GbParams& p, const GbOut& o, cudaStream_t st);
-// Partitioned variant: offsets from the histogram, then per-partition tables.
-rel_status gb_launch_part_scan(const GbParams& p, cudaStream_t st);
+// Partitioned variant: partition starts (and, with cta_offsets, every CTA's
+// offset inside each partition) from the histogram, then per-partition tables.
+rel_status gb_launch_part_scan(const GbParams& p, bool cta_offsets, cudaStream_t st);
 rel_status gb_launch_part_agg(const GbParams& p, int shape, const GbOut& o, cudaStream_t st);
 // Streaming kernel for key/value shapes (stream.cu): pinned keys and/or a
 // small shared table in front of the global table, no staging ring.
