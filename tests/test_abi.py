@@ -308,3 +308,20 @@ def test_numpy_layouts_match_ctypes(ct):
     assert dt.itemsize == ctypes.sizeof(ct)
     for name, _ in ct._fields_:
         assert dt.fields[name][1] == getattr(ct, name).offset, name
+
+
+def test_partitioned_workspace_holds_both_record_levels(L):
+    # one 16-byte record per row, and above 2^8 partitions a second one per
+    # row for the first scatter level (bins of partitions)
+    n = 1_000_000
+    sizes = {}
+    for bits in (4, 8, 9, 14):
+        plan = rel.Plan()
+        plan.variant, plan.slots, plan.part_bits, plan.smem_slots = rel.VAR_PARTITIONED, 1 << 16, bits, 1024
+        sizes[bits] = L.rel_plan_ws_bytes(ctypes.byref(plan), 4, n)
+    assert 16 * n < sizes[4] <= sizes[8] < 16 * n + (1 << 26)
+    assert sizes[9] - sizes[8] >= 16 * n
+    assert sizes[14] - sizes[9] < (1 << 26)  # only per-partition arrays grow
+    plan = rel.Plan()
+    plan.variant, plan.slots, plan.part_bits = rel.VAR_PARTITIONED, 1 << 16, 15
+    assert L.rel_plan_ws_bytes(ctypes.byref(plan), 4, n) == 0  # beyond 16384 partitions
