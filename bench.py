@@ -691,7 +691,7 @@ def run_lineitem_scale(args, dev, peak_gbs):
     out = {"rows": n, "bytes": nbytes, "kernel": main_k, "ms_per_launch": ms, "algo_gbs": gbs,
            "frac": gbs / peak_gbs, "frac_nominal": gbs / NOMINAL_HBM_GBS,
            "rows_per_s": n / (ms / 1e3), "groups": int(plan.est_groups),
-           "plan": "exact distinct count + sketch pins (registers)"}
+           "plan": "exact distinct count + sketch pins (thread-private shared words)"}
     del q
     torch.cuda.empty_cache()
     return out

@@ -636,12 +636,15 @@ rel_status set_layers(GbParams& p, const rel_plan* plan, int shape) {
              REL_E_INVALID;
     p.tiny_frozen = 1;
     p.tiny_probes = 1;
-    // few pinned keys, no CTA-shared layer, a shape of <= 5 words: keep the
-    // accumulators in registers (dense ids in slot order)
+    // at most four pinned keys, no CTA-shared layer, a shape of <= 5 words:
+    // keep the accumulators in registers (dense ids in slot order).  With
+    // more keys the register file costs more than it saves: 1e8 lineitem
+    // rows with 6 pinned groups x 5 words take 1.49 ms in registers (132 of
+    // them, one 9-warp CTA per SM) and 0.96 ms in thread-private shared words
     const bool regs_shape = shape == SHAPE_Q1 || shape == SHAPE_KV4_64 || shape == SHAPE_KV4_32 ||
                             shape == SHAPE_KV2_64 || shape == SHAPE_KV2_32;
-    if (regs_shape && p.smem_slots == 0 && plan->n_hot <= 8 && p.tiny_slots <= 16) {
-      p.tiny_ns = plan->n_hot <= 4 ? 4u : 8u;
+    if (regs_shape && p.smem_slots == 0 && plan->n_hot <= 4 && p.tiny_slots <= 16) {
+      p.tiny_ns = 4u;
       p.tiny_dense = 0;
       uint64_t j = 0;
       for (uint32_t s = 0; s < p.tiny_slots; ++s)

@@ -11,7 +11,8 @@ CASE (inputs seeded and synthetic, as in the bench):
   stream    streaming group-by of 5e7 four-key rows with pinned keys (gb_stream)
   join      join build of 1e6 unique keys and probe of 1.6e7 keys (90 % hits)
   lineitem  fused filter + group-by of 2e7 lineitem rows: exact count (staged
-            key set), sketch, register-privatised aggregation, compaction
+            key set), sketch, aggregation in thread-private shared words,
+            compaction
   mlp       planner network forward, backward and AdamW on a batch of 256
   batch     a batch of 512 group-bys and 64 join partitions (the batched
             workload's recipe, rows divided by 8): the two persistent launches
@@ -100,7 +101,7 @@ def case_lineitem(n=20_000_000):
     rel.groupby(q, plan=p)
     used = set(q["keys"]) | {c[0] for c in q.get("preds", [])}
     return {"gb_main_staged_keyset": (n, "rows", sum(q["cols"][c].nbytes for c in used)),
-            "gb_main_regs": (n, "rows", sum(c.nbytes for c in q["cols"])),
+            "gb_main_layered": (n, "rows", sum(c.nbytes for c in q["cols"])),
             "sketch": (1, "sketch", None)}
 
 
