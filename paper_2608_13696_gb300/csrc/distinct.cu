@@ -175,6 +175,9 @@ __global__ void __launch_bounds__(DS_BLOCK, 3) distinct_k(const __grid_constant_
     uint32_t ok;
     if (vec) load_chunk<KT, true>(keys, n, base, ek, ok);
     else load_chunk<KT, false>(keys, n, base, ek, ok);
+    // the set's overflow flag, read now and tested after the chunk (its
+    // latency hides behind the chunk's work)
+    const uint32_t ovf = lane == 0 ? ld_relaxed_u32(&p.hdr->overflow) : 0u;
     uint32_t need = 0;
 #pragma unroll
     for (int j = 0; j < DS_U; ++j) {
@@ -235,8 +238,7 @@ __global__ void __launch_bounds__(DS_BLOCK, 3) distinct_k(const __grid_constant_
     if (bad) atomicOr(&p.hdr->overflow, 1u);
     // once the set overflowed the count is void (the caller retries with more
     // room): stop reading, uniformly per warp
-    const uint32_t f = (threadIdx.x & 31) == 0 ? ld_relaxed_u32(&p.hdr->overflow) : 0u;
-    if (__shfl_sync(0xffffffffu, f, 0)) break;
+    if (__shfl_sync(0xffffffffu, ovf, 0) || __any_sync(0xffffffffu, bad)) break;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
