@@ -101,3 +101,19 @@ def test_two_level_scatter(bits):
         plan.smem_slots = max(256, min(4096, 1 << (20 - bits)))
 
     run(oracle.kv_query(keys, vals), rel.PLAN_EXACT | rel.PLAN_SKETCH, force)
+
+
+@pytest.mark.parametrize("ops,key_dtype", [(("sum", "count"), np.int64), (("count", "sum"), np.int32),
+                                           (("max", "min", "count", "sum"), np.int32)])
+def test_two_level_scatter_pinned_shapes(ops, key_dtype):
+    # pinned heavy hitters with both aggregate widths and both key types,
+    # through the two scatter levels (2^10 partitions)
+    keys, vals = synth.zipf_kv(700_001, seed=31, n_ranks=250_000)
+    keys = keys.astype(key_dtype)
+
+    def force(plan):
+        plan.part_bits = 10
+        plan.smem_slots = 1024
+
+    plan = run(oracle.kv_query(keys, vals, ops=ops), rel.PLAN_EXACT | rel.PLAN_SKETCH, force)
+    assert plan.n_hot > 0
