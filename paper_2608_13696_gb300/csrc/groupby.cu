@@ -993,7 +993,9 @@ __device__ __forceinline__ void part_insert(const GbParams& p, uint64_t* tk, uns
   gtab_update<S>(p, ek, x);
 }
 
-constexpr int PA_R = 4;  // record groups in flight per warp in the aggregation pass
+// record groups in flight per warp in the aggregation pass (2, 4, 8: 1.36, 1.40
+// and 1.94 ms on 2e8 Zipf rows: fewer registers, more warps)
+constexpr int PA_R = 2;
 
 // Pass 3: each CTA aggregates whole partitions in a shared-memory table of
 // p.smem_slots slots and writes their groups straight to the output (warp
